@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 RLB time step: G velocity-node updates/s on the relaxation-time sweep.
+
+Workload (default ``sweep``): the paper's Sod tube, (P, n, v) = (1, 1, 0) | (0.1, 0.125, 0) on [-0.5, 0.5],
+Nx = 4096, Qp = 3, tau in {1e-4, 1e-3, 1e-2, 1e-1, 1, 10, inf} x Qxi in {8, 32, 128, 200}: 28 tubes, 31.65 M
+velocity nodes, all advanced together, one handle, FP64. A step is one SSP-RK3 time step of every tube
+(three launches of the stage kernel). One velocity-node update = one velocity at one cell over one step.
+
+    python bench.py [--steps K] [--warmup W] [--workload sweep|small|stress] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun every rank advances its own copy of the workload (weak scaling, no
+collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1608_03004_gb300 import workloads as W  # noqa: E402
+
+METRIC = "G velocity-node updates/s"
+UNIT = "G updates/s"
+# Algorithmic FP64 flops per velocity-node per RK stage (FMA = 2): WENO5 interface value 54, flux
+# difference and xi/dx 2, equilibrium (Nv+1 = 6 FMAs) 12, collision 5, Runge-Kutta combination 5, moment
+# reduction 6. Per-cell work (Landau solve, Legendre series) is not counted, so this is a lower bound.
+FLOPS_PER_NODE_STAGE = 84
+# Algorithmic HBM bytes per velocity node per step with one launch per stage: stage inputs read once
+# (1 + 2 + 2 doubles), outputs written once (3 doubles).
+BYTES_PER_NODE_STEP = 64
+PROFILE = os.path.join(ROOT, "profiles", "rlb_stage_kernel_sod_sweep.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1608_03004_gb300", "csrc", "rlb.cu")
+
+
+def workload(name: str):
+    if name == "sweep":
+        return W.sod_sweep(), ("Sod tube sweep: Nx=4096, tau in {1e-4,1e-3,1e-2,1e-1,1,10,inf} x Qxi in "
+                               "{8,32,128,200}, Qp=3, Np=2, Nv=5, CFL 0.5 (dt=min(0.5dx,1.25tau)), open BC")
+    if name == "small":
+        return W.sod_small(), "Sod tube: Nx=400, Qp=3, Qxi=8, tau=1e-3, CFL 0.5, open BC"
+    if name == "stress":
+        return [W.stress()], "Sod tube: Nx=1048576, Qp=3, Qxi=128, tau=1e-2, CFL 0.5, open BC"
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if _num(r[0])]
+        mx = [float(r[1]) for r in self.rows if _num(r[1])]
+        reasons = set()
+        for r in self.rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 r[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _num(s: str) -> bool:
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# ---------------------------------------------------------------------------------------------------------
+# oracle on the host cores (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------------------------------------
+
+def _oracle_worker(conn, specs):
+    """Holds the oracle states of its tubes; each 'step' message advances them by one time step."""
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    params, states = [], []
+    for s in specs:
+        tau = s.tau if (s.tau is not None and math.isfinite(s.tau)) else 0.0
+        p = oracle.Params(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, tau, s.bc)
+        params.append(p)
+        states.append(oracle.init_riemann(p, s.left, s.right, s.x_left))
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg == "stop":
+            break
+        t0 = time.perf_counter()
+        for k, p in enumerate(params):
+            states[k] = oracle.step(p, states[k], 1)
+        conn.send(time.perf_counter() - t0)
+
+
+class OraclePool:
+    """Static partition of the tubes over worker processes (spawned: no fork after CUDA initialisation)."""
+
+    def __init__(self, specs, nproc: int):
+        import oracle
+
+        oracle.build()  # once, before the workers load it
+        nproc = max(1, min(nproc, len(specs)))
+        groups = [[] for _ in range(nproc)]
+        load = [0] * nproc
+        for s in sorted(specs, key=lambda s: -s.Nx * s.Q):  # greedy balance by velocity nodes
+            k = load.index(min(load))
+            groups[k].append(s)
+            load[k] += s.Nx * s.Q
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for g in groups:
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, g), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            assert c.recv() == "ready"
+        self.nproc = nproc
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send("step")
+        for c in self.conns:
+            c.recv()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for c in self.conns:
+            c.send("stop")
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(specs, desc: str) -> dict:
+    pool = OraclePool(specs, host_cores())
+    try:
+        wall = pool.step()
+    finally:
+        pool.close()
+    nodes = W.total_nodes(specs)
+    return {"value": nodes / wall / 1e9, "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
+            "sample": f"one time step of every tube of the workload ({nodes} velocity nodes) from the initial "
+                      f"condition, plain C FP64 oracle, tubes split over {pool.nproc} processes",
+            "seconds": wall}
+
+
+# ---------------------------------------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------------------------------------
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def ncu_traffic_per_launch():
+    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on the current kernel."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_stage_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_tr or m_sha.group(1) != sha:
+        return None
+    return float(m_tr.group(1))
+
+
+# ---------------------------------------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------------------------------------
+
+def run_reference(args, specs, desc, rank):
+    if rank != 0:
+        return
+    pool = OraclePool(specs, host_cores())
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        times = [pool.step() for _ in range(args.steps)]
+    finally:
+        pool.close()
+    nodes = W.total_nodes(specs)
+    total = sum(times)
+    value = nodes * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "velocity_nodes_per_step": nodes},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
+                             "sample": f"each step: one time step of every tube ({nodes} velocity nodes), plain C "
+                                       f"FP64 oracle, tubes split over {pool.nproc} processes"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, specs, desc, rank, world):
+    import torch
+
+    from paper_1608_03004_gb300 import binding as rb
+
+    dev = torch.cuda.current_device()
+    tubes = [rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, s.tau, s.bc, 0) for s in specs]
+    states = np.array([list(s.left) + list(s.right) for s in specs])
+    xl = np.array([s.x_left for s in specs])
+    stream = torch.cuda.current_stream()
+    nodes = W.total_nodes(specs)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    h = rb.rlb_init_riemann(tubes, states, xl, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        rb.rlb_step(h, 1)
+    rb.rlb_sync(h)
+    torch.cuda.synchronize()
+    barrier()
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    clocks = ClockSampler(int(visible[dev]) if dev < len(visible) and visible[dev].isdigit() else dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        rb.rlb_step(h, 1)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    rb.rlb_sync(h)  # raises if any cell went non-physical during the timed steps
+
+    # end to end through the public API with host buffers: H2D of the state from pinned memory, one step,
+    # D2H of the fields, every step
+    e2e_steps = max(3, min(args.steps, 10))
+    host_state = torch.empty(h.state_size, dtype=torch.float64, pin_memory=True).numpy()
+    host_fields = torch.empty((rb.NFIELDS, h.nx_total), dtype=torch.float64, pin_memory=True).numpy()
+    rb.rlb_get_state(h, host_state)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rb.rlb_set_state(h, host_state)
+        rb.rlb_step(h, 1)
+        rb.rlb_moments(h, host_fields)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    rb.rlb_destroy(h)
+
+    value = world * nodes * args.steps / (total_ms * 1e-3) / 1e9
+    stage_ms = total_ms / (3 * args.steps)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    # FP64: 2 DFMA per SM per clock on GB300 (measured with a DFMA loop: 1.90 per SM-clock at an assumed 2070
+    # MHz, i.e. 1.2 TFLOP/s; nominal 1.25 TFLOP/s), 4 flops per SM per clock
+    fp64_peak = props.multi_processor_count * 4 * sm_max * 1e6 / 1e12
+    achieved = FLOPS_PER_NODE_STAGE * nodes / (stage_ms * 1e-3) / 1e12
+    hbm_peak = peaks.get("hbm_gbs", 6682.2)
+    hbm_achieved = BYTES_PER_NODE_STEP * nodes / 3 / (stage_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "velocity_nodes_per_step": nodes, "tubes": len(specs),
+                   "l2": "inputs larger than L2: state 8 B x nodes = %.0f MB per buffer, 3 buffers; no flush"
+                         % (8 * nodes / 1e6),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": ncu_traffic_per_launch(),
+                     "kernel": "rlb_stage_kernel", "launch_ms": stage_ms,
+                     "note": "FP64 pipe bound; peak = SMs x 2 DFMA/clk x 2 flops x max SM clock (derived); "
+                             f"algorithmic {FLOPS_PER_NODE_STAGE} FP64 flops per velocity node per stage"},
+        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak, "frac": hbm_achieved / hbm_peak,
+                "note": f"{BYTES_PER_NODE_STEP} algorithmic bytes per velocity node per step, of measured copy"},
+        "e2e": {"value": world * nodes * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * h.state_size, "d2h_bytes_per_step": 8 * rb.NFIELDS * h.nx_total,
+                "steps": e2e_steps, "api": "rlb_set_state(host) + rlb_step(1) + rlb_moments(host)"},
+        "clocks": clk,
+        "gpu_launches": 3 * args.steps,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(specs, desc)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["sweep", "small", "stress"], default="sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    specs, desc = workload(args.workload)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, specs, desc, rank)
+        return
+    import torch
+
+    if world > 1:
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    try:
+        run_ours(args, specs, desc, rank, world)
+    finally:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+/*
+ * rlb.h - C ABI of the GB300 (sm_103a) time step of the quadrature-based finite-difference relativistic
+ * lattice Boltzmann model for massless particles (Blaga & Ambrus, arXiv:1608.03004).
+ *
+ * The library advances one or more independent one-dimensional tubes ("shock tubes") of the kinetic
+ * equation (section "Relativistic lattice Boltzmann equation", Eq. (Boltz)):
+ *     (d_t + xi d_x) f = -(u^0 - xi u^x)/tau (f - f^eq),
+ * with the Anderson-Witting collision, the Landau-frame equilibrium rebuilt every stage from the
+ * stress-energy tensor T^{mu nu} (second moment of f), the truncated Maxwell-Juttner expansion of
+ * Eq. (feqtrunc), fifth-order WENO advection and third-order SSP Runge-Kutta time integration (section
+ * "Numerical results").
+ *
+ * Conventions shared by every entry point
+ *  - Velocities: s = i*Qxi + j pairs the i-th zero pbar_i of the generalised Laguerre polynomial
+ *    L^(1)_Qp (radial, momentum magnitude p/T0, T0 = 1) with the j-th zero xi_j of the Legendre
+ *    polynomial P_Qxi (direction cosine along x), both ascending (section "Discretization of the momentum
+ *    space using quadrature rules"). The paper's z axis is called x here.
+ *  - Stored population: F_s(x) = 2 pi w^p_i w^xi_j exp(pbar_i) f(x, pbar_i, xi_j), so that
+ *    N^0 = sum_s F pbar, N^x = sum F pbar xi, T^00 = sum F pbar^2, T^0x = sum F pbar^2 xi,
+ *    T^xx = sum F pbar^2 xi^2.
+ *  - Packed state layout ("packed"): tubes one after the other; tube b holds Q_b rows of Nx_b doubles
+ *    (row s, cell x at offset s*Nx_b + x). Fields layout: [RLB_NFIELDS][sum_b Nx_b], each field row holding
+ *    the tubes' cells one after the other.
+ *  - Pointers flagged "on_device" are CUDA device pointers on the handle's device, otherwise host
+ *    pointers (pageable or pinned). Caller buffers are never retained after a call returns.
+ *  - Every call is ordered on the stream given to rlb_init. Calls that copy to the host wait for that
+ *    stream. Errors are returned, never aborted on. A cell that reaches a non-physical state (e <= 0,
+ *    |v| >= 1, n <= 0 or NaN) sets a sticky device flag; the next call that synchronises (rlb_moments,
+ *    rlb_get_state, rlb_sync) returns RLB_ENONPHYS.
+ *  - Limits: 1 <= Np < Qp <= 4, 2 <= Nv <= 8, 2*Qxi >= Nv + 3 (exact recovery of T^{mu nu}, Eq. (mom_feq)),
+ *    Qxi <= 1024, Nx >= 1 (periodic: Nx >= 3), dx > 0, dt > 0.
+ */
+#ifndef RLB_H
+#define RLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlb_ctx *rlb_handle;
+
+typedef enum {
+  RLB_OK = 0,
+  RLB_EINVAL = 1,   /* an argument is out of range or a pointer is NULL */
+  RLB_ENOMEM = 2,   /* a device or host allocation failed */
+  RLB_ECUDA = 3,    /* a CUDA runtime call failed */
+  RLB_ENONPHYS = 4  /* some cell reached a non-physical state since the last check */
+} rlb_status;
+
+enum { RLB_BC_OPEN = 0, RLB_BC_PERIODIC = 1 };
+
+/* Fields written by rlb_moments, in this order. */
+enum {
+  RLB_F_N0 = 0, RLB_F_NX, RLB_F_T00, RLB_F_T0X, RLB_F_TXX, RLB_F_E, RLB_F_V, RLB_F_N, RLB_NFIELDS
+};
+
+/* One tube. tau <= 0 or tau = +inf means the ballistic regime (no collision). */
+typedef struct {
+  int32_t Qp;       /* radial Gauss-Laguerre order (the paper uses 3) */
+  int32_t Qxi;      /* polar Gauss-Legendre order */
+  int32_t Np;       /* radial truncation order of f^eq (the paper uses 2) */
+  int32_t Nv;       /* angular truncation order of f^eq (the paper uses 5) */
+  int64_t Nx;       /* number of cells */
+  double dx;        /* cell width; cell c has its centre at x_left + (c + 1/2) dx */
+  double dt;        /* time step */
+  double tau;       /* relaxation time */
+  int32_t bc;       /* RLB_BC_OPEN (zero-gradient ghosts, section "Riemann problem") or RLB_BC_PERIODIC */
+  int32_t reserved; /* must be 0 */
+} rlb_tube;
+
+/*
+ * rlb_init - create a handle for ntubes tubes and set F to the truncated equilibrium of a per-cell state.
+ *   Initial condition, Eq. (condinit): F_s(x) = F^eq_s(P(x), n(x), v(x)) with T = P/n.
+ *   P, n, v: per-cell pressure, density and velocity, each sum_b Nx_b doubles (tubes one after the
+ *   other), host pointers or, with ic_on_device != 0, device pointers. stream: a cudaStream_t (NULL =
+ *   default stream). The handle owns all device memory it allocates; rlb_destroy frees it.
+ *   Returns RLB_EINVAL for bad orders/sizes or a non-positive P or n, RLB_ENOMEM, RLB_ECUDA.
+ */
+rlb_status rlb_init(rlb_handle *out, const rlb_tube *tubes, int32_t ntubes, const double *P, const double *n,
+                    const double *v, int32_t ic_on_device, void *stream);
+
+/*
+ * rlb_init_riemann - as rlb_init for the Riemann problem of Eq. (condinit): per tube b,
+ *   states[6b..6b+5] = (P_L, n_L, v_L, P_R, n_R, v_R) and x_left[b] is the left edge of the domain. Cells
+ *   whose centre is left of x = 0 take the left equilibrium, right of it the right one, and a centre at
+ *   exactly x = 0 the mean of the two. states and x_left are host arrays.
+ */
+rlb_status rlb_init_riemann(rlb_handle *out, const rlb_tube *tubes, int32_t ntubes, const double *states,
+                            const double *x_left, void *stream);
+
+/*
+ * rlb_step - advance every tube by nsteps time steps of SSP-RK3 (three stages per step), each stage
+ *   computing moments, Landau frame, f^eq, collision and WENO5 advection (section "Numerical results",
+ *   Eq. (Boltz)). Asynchronous on the handle's stream; nsteps >= 0. Returns RLB_EINVAL for a NULL handle
+ *   or negative nsteps, RLB_ECUDA if a launch fails.
+ */
+rlb_status rlb_step(rlb_handle h, int64_t nsteps);
+
+/*
+ * rlb_moments - write the macroscopic fields of the current state (section "Relativistic lattice
+ *   Boltzmann equation"): N^0, N^x, T^00, T^0x, T^xx, the Landau-frame energy density e, velocity v and
+ *   density n = -u_mu N^mu, as [RLB_NFIELDS][sum_b Nx_b] doubles into out (device pointer if
+ *   out_on_device, else host; a host copy waits for the stream). Returns RLB_ENONPHYS if the sticky flag
+ *   is set (the fields are still written).
+ */
+rlb_status rlb_moments(rlb_handle h, double *out, int32_t out_on_device);
+
+/* rlb_get_state / rlb_set_state - copy F out of / into the handle in the packed layout (checkpoint and
+ *   restore). F holds rlb_state_size() doubles; host or device pointer as flagged. */
+rlb_status rlb_get_state(rlb_handle h, double *F, int32_t on_device);
+rlb_status rlb_set_state(rlb_handle h, const double *F, int32_t on_device);
+
+/* rlb_sync - wait for the handle's stream; returns RLB_ENONPHYS (and clears the flag) if it was set. */
+rlb_status rlb_sync(rlb_handle h);
+
+/* rlb_destroy - free the handle and its device memory (after waiting for its stream). NULL is a no-op. */
+rlb_status rlb_destroy(rlb_handle h);
+
+/* rlb_state_size - number of doubles in the packed state of a handle (sum_b Qp_b Qxi_b Nx_b). */
+int64_t rlb_state_size(rlb_handle h);
+
+/* rlb_error_string - static, human-readable name of a status. */
+const char *rlb_error_string(rlb_status s);
+
+/*
+ * rlb_suggest_dt - time step min(cfl * dx, 1.25 tau): the CFL limit for speeds |xi| <= 1 (section
+ *   "Numerical results": "the time step is limited by the CFL condition"; cfl = 0.5 gives the paper's
+ *   dt = 0.5e-4 at dx = 1e-4) and the SSP-RK3 stability limit of the stiff collision term for |v| <= 0.6.
+ *   tau <= 0 or infinite: cfl * dx.
+ */
+double rlb_suggest_dt(double dx, double tau, double cfl);
+
+/*
+ * rlb_quadrature - the library's own nodes and weights (host, FP64): pbar[Qp], wp[Qp] for the generalised
+ *   Gauss-Laguerre rule with weight pbar e^-pbar, xi[Qxi], wxi[Qxi] for Gauss-Legendre, both ascending
+ *   (section "Discretization of the momentum space using quadrature rules").
+ */
+rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double *pbar, double *wp, double *xi, double *wxi);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLB_H */

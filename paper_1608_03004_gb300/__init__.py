@@ -1,0 +1,31 @@
+"""GB300-native (sm_103a) time step of the quadrature-based finite-difference relativistic lattice Boltzmann
+model for massless particles (Blaga & Ambrus, arXiv:1608.03004).
+
+The compute path is the CUDA library ``librlb.so`` (sources in ``csrc/``, C ABI in ``include/rlb.h``);
+``binding`` exposes its entry points under the same names. ``workloads`` holds the seeded synthetic inputs.
+Importing this package loads nothing; the library is loaded on the first call and a missing library is an
+error, never a fallback.
+"""
+from .binding import (  # noqa: F401
+    BC_OPEN,
+    BC_PERIODIC,
+    FIELDS,
+    NFIELDS,
+    Handle,
+    RlbError,
+    Tube,
+    library_path,
+    load,
+    rlb_destroy,
+    rlb_error_string,
+    rlb_get_state,
+    rlb_init,
+    rlb_init_riemann,
+    rlb_moments,
+    rlb_quadrature,
+    rlb_set_state,
+    rlb_state_size,
+    rlb_step,
+    rlb_suggest_dt,
+    rlb_sync,
+)

@@ -1,0 +1,888 @@
+// GB300 (sm_103a) CUDA implementation of the time step of the quadrature-based finite-difference
+// relativistic lattice Boltzmann model for massless particles (Blaga & Ambrus, arXiv:1608.03004), and
+// its C ABI (include/rlb.h).
+//
+// One SSP-RK3 stage is one launch of rlb_stage_kernel over every tile of every tube. A CTA owns a tile of
+// TX = 63 cells of one tube and, for those cells:
+//   A. reduces F over all Q velocities to N^0, N^x, T^00, T^0x, T^xx (section "Relativistic lattice
+//      Boltzmann equation");
+//   B. solves the Landau-frame eigenproblem T^mu_nu u^nu = -e u^mu for e, v, n and builds the per-cell
+//      coefficients of the truncated equilibrium of Eq. (feqtrunc);
+//   C. walks the velocity rows four at a time: stages the row (tile + 3-cell halo, boundary condition
+//      folded into the load) in shared memory, reconstructs the 64 interface values with WENO5 and writes
+//      F_out = a F^n + b (F_in + dt L(F_in)), L = advection + Anderson-Witting collision (Eq. (Boltz)).
+// The step is FP64 throughout; on GB300 the FP64 pipe (about 2 DFMA per SM per clock) bounds it, so the
+// arithmetic is arranged to spend as few FP64 instructions per velocity-node update as possible.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/rlb.h"
+#include "rlb_internal.h"
+
+using namespace rlb;
+
+namespace {
+
+constexpr int NT = 256;                    // threads per CTA
+constexpr int GW = 64;                     // threads per velocity group (one row at a time)
+constexpr int NG = NT / GW;                // velocity rows processed together
+constexpr int TX = GW - 1;                 // cells per tile: GW interfaces bound TX cells
+constexpr int HALO = 3;                    // WENO5 reaches three cells upwind/downwind
+constexpr int RW = TX + 2 * HALO;          // staged row length
+constexpr int NBC = QP_MAX * (NV_MAX + 1); // per-cell equilibrium coefficients
+constexpr double WENO_EPS = 1e-6;
+
+// Series tables for the Legendre coefficients of (1 - beta xi)^-m (filled once per device):
+//   g_ic[r][k] = (2k+1)/2 * int_{-1}^{1} xi^r P_k(xi) dxi,   g_cb[m][r] = C(m + r - 1, r).
+__device__ double g_ic[(R_MAX + 1) * (NV_MAX + 1)];
+__device__ double g_cb[(M_MAX + 1) * (R_MAX + 1)];
+
+struct StageArgs {
+  const TubeDev* tubes;
+  const int2* tiles;  // (tube, first cell)
+  const double* Fn;   // state at the start of the step (read at the cell only)
+  const double* Fin;  // stage input (read with halo)
+  double* Fout;       // stage output
+  const double* tab;
+  int* flag;
+  double a, b;        // Shu-Osher combination F_out = a F^n + b (F_in + dt L(F_in))
+};
+
+// --------------------------------------------------------------------------------------------------
+// Device helpers
+// --------------------------------------------------------------------------------------------------
+
+// Source cell of a staged position x in [-HALO, Nx - 1 + GW + HALO]: periodic wrap (Nx >= 3) or zero-gradient
+// ghosts (open boundary). Always in [0, Nx).
+__device__ __forceinline__ int map_cell(int x, int Nx, int bc) {
+  if (bc == RLB_BC_PERIODIC) {
+    if (x < 0) x += Nx;
+    return x % Nx;
+  }
+  return x < 0 ? 0 : (x >= Nx ? Nx - 1 : x);
+}
+
+// Landau frame from (N0, Nx, T00, T0x, Txx): e, beta, n (Landau), T. Returns false if non-physical.
+__device__ __forceinline__ bool landau(const double mom[5], double& e, double& beta, double& n, double& T) {
+  const double A = mom[2] + mom[4];
+  const double disc = A * A - 4.0 * mom[3] * mom[3];
+  e = 0.5 * ((mom[2] - mom[4]) + sqrt(disc));
+  beta = mom[3] / (mom[4] + e);
+  const double gam = 1.0 / sqrt(1.0 - beta * beta);
+  n = gam * (mom[0] - beta * mom[1]);
+  T = e / (3.0 * n);
+  return disc >= 0.0 && e > 0.0 && fabs(beta) < 1.0 && n > 0.0 && T > 0.0;
+}
+
+// WENO5 interface value from five samples ordered along the wind (v2 is the upwind cell next to the
+// interface). Same scheme as Jiang & Shu: candidates (2,-7,11)/6, (-1,5,2)/6, (2,5,-1)/6, smoothness
+// indicators with weights 13/12 and 1/4, linear weights (1, 6, 3)/10, alpha_k = d_k/(eps + beta_k)^2.
+// Written on the first differences d_l: 3 beta_k is the quadratic form (4x^2 - 11xy + 10y^2,
+// 4x^2 - 5xy + 4y^2, 10x^2 - 11xy + 4y^2) of adjacent differences, and the common factors of the alphas
+// are cancelled so that only one division remains.
+__device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4) {
+  const double d1 = v1 - v0, d2 = v2 - v1, d3 = v3 - v2, d4 = v4 - v3;
+  const double q1 = d1 * d1, q2 = d2 * d2, q3 = d3 * d3, q4 = d4 * d4;
+  const double p12 = d1 * d2, p23 = d2 * d3, p34 = d3 * d4;
+  const double E = 3.0 * WENO_EPS;
+  const double u0 = fma(4.0, q1, fma(-11.0, p12, fma(10.0, q2, E)));
+  const double u1 = fma(4.0, q2, fma(-5.0, p23, fma(4.0, q3, E)));
+  const double u2 = fma(10.0, q3, fma(-11.0, p34, fma(4.0, q4, E)));
+  const double s0 = u0 * u0, s1 = u1 * u1, s2 = u2 * u2;
+  const double a0 = s1 * s2, a1 = 6.0 * (s0 * s2), a2 = 3.0 * (s0 * s1);
+  const double r0 = fma(5.0, d2, -2.0 * d1), r1 = fma(2.0, d3, d2), r2 = fma(5.0, d3, -d4);
+  const double num = fma(a0, r0, fma(a1, r1, a2 * r2));
+  return v2 + num / (6.0 * (a0 + a1 + a2));
+}
+
+// --------------------------------------------------------------------------------------------------
+// Per-cell equilibrium coefficients of a tile (shared by the stage and initial-condition kernels)
+// --------------------------------------------------------------------------------------------------
+
+struct CoefSmem {
+  double hh[M_MAX - 1][NV_MAX + 1][GW];  // hhat_{m,k}, m = 2 .. Np+2
+  double cell[3][GW];                    // n, T, beta of each cell
+  int ok[GW];
+};
+
+// One parity class of the Legendre coefficients hhat_{m,k} = (2k+1)/2 int P_k(xi) (1 - beta xi)^-m dxi,
+// m = 2..NPc+2, k = PAR, PAR+2, .. <= NVc, by the positive power series (1 - beta xi)^-m =
+// sum_r C(m+r-1, r) beta^r xi^r with int xi^r P_k tabulated. Terms of one class share one sign, so the sum
+// has no cancellation; it stops when the largest-m term drops below 1e-18 (1 - beta^2).
+template <int NPc, int NVc, int PAR>
+__device__ bool hhat_parity(double beta, double* hh_col /* [m-2][k][GW] at this cell */) {
+  constexpr int NK = (NVc - PAR) / 2 + 1;
+  double acc[NPc + 1][NK];
+#pragma unroll
+  for (int m = 0; m <= NPc; ++m)
+#pragma unroll
+    for (int q = 0; q < NK; ++q) acc[m][q] = 0.0;
+  bool done = (beta == 0.0);
+  if (beta == 0.0 && PAR == 0) {
+#pragma unroll
+    for (int m = 0; m <= NPc; ++m) acc[m][0] = 1.0;
+  }
+  if (!done) {
+    const double b2 = beta * beta;
+    const double tol = 1e-18 * (1.0 - b2);
+    double br = PAR ? beta : 1.0;  // beta^r
+    for (int r = PAR; r <= R_MAX; r += 2) {
+      const double* ic = g_ic + r * (NV_MAX + 1);
+      double tlast = 0.0;
+#pragma unroll
+      for (int m = 0; m <= NPc; ++m) {
+        const double t = g_cb[(m + 2) * (R_MAX + 1) + r] * br;
+#pragma unroll
+        for (int q = 0; q < NK; ++q) acc[m][q] = fma(ic[PAR + 2 * q], t, acc[m][q]);
+        tlast = t;
+      }
+      if (r >= NVc && fabs(tlast) < tol) {
+        done = true;
+        break;
+      }
+      br *= b2;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m <= NPc; ++m)
+#pragma unroll
+    for (int q = 0; q < NK; ++q) hh_col[((m * (NV_MAX + 1)) + PAR + 2 * q) * GW] = acc[m][q];
+  return done;
+}
+
+// Fill B[i (NV_MAX+1) + k][c] for the TX cells of a tile from cs.cell (n, T, beta) and cs.ok:
+//   F^eq_ij = sum_k B[i][k] w^xi_j P_k(xi_j),  B[i][k] = n/(4T^3) w^p_i sum_q s^(q+2) K[i][q] hhat_{q+2,k},
+// s = T/gamma (Eq. (feqtrunc): Laguerre generating function for the radial projection, Legendre projection
+// of each (1 - beta xi)^-m for the angular one). Groups 0/1 run the even/odd series, then group g builds
+// radial row i = g. Cells with ok == 0 get B = 0. Ends with a barrier.
+template <int NPc, int NVc>
+__device__ void tile_coeffs(const double* tab, int Qp, CoefSmem& cs, double (*Bs)[GW], int* flag) {
+  const int c = threadIdx.x % GW, g = threadIdx.x / GW;
+  if (g < 2 && c < TX) {
+    const double beta = cs.cell[2][c];
+    bool conv = true;
+    if (cs.ok[c]) {
+      if (g == 0)
+        conv = hhat_parity<NPc, NVc, 0>(beta, &cs.hh[0][0][c]);
+      else
+        conv = hhat_parity<NPc, NVc, 1>(beta, &cs.hh[0][0][c]);
+    }
+    if (!conv) {
+      cs.ok[c] = 0;  // both groups may write 0; no other value is written concurrently
+      atomicOr(flag, 1);
+    }
+  }
+  __syncthreads();
+  if (c < TX) {
+    const int i = g;
+    double B[NVc + 1];
+#pragma unroll
+    for (int k = 0; k <= NVc; ++k) B[k] = 0.0;
+    if (i < Qp && cs.ok[c]) {
+      const double n = cs.cell[0][c], T = cs.cell[1][c], beta = cs.cell[2][c];
+      const double s = T * sqrt(1.0 - beta * beta);
+      const double pref = n / (4.0 * T * T * T) * tab[TAB_WP + i];
+      double sq = s * s;
+#pragma unroll
+      for (int q = 0; q <= NPc; ++q) {
+        const double G = pref * sq * tab[TAB_K + i * (NP_MAX + 1) + q];
+#pragma unroll
+        for (int k = 0; k <= NVc; ++k) B[k] = fma(G, cs.hh[q][k][c], B[k]);
+        sq *= s;
+      }
+    }
+    if (i < QP_MAX) {
+#pragma unroll
+      for (int k = 0; k <= NVc; ++k) Bs[i * (NV_MAX + 1) + k][c] = B[k];
+    }
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------------------------------
+// Stage kernel
+// --------------------------------------------------------------------------------------------------
+
+struct StageSmem {
+  union {
+    double red[NG][5][GW];
+    CoefSmem coef;
+  } u;
+  double B[NBC][GW];
+  double rate[2][GW];
+  double row[2][NG][RW + 3];
+  double phi[2][NG][GW];
+  int src[RW + 3];  // source cell of each staged position (boundary condition applied)
+};
+
+template <int NPc, int NVc>
+__device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSmem& sm) {
+  const int tid = threadIdx.x, c = tid % GW, g = tid / GW;
+  const double* tab = A.tab + T.tab;
+  const int Qp = T.Qp, Qxi = T.Qxi, Q = Qp * Qxi, Nx = T.Nx, ld = T.ld;
+  const double* Fin = A.Fin + T.off;
+  const double* Fn = A.Fn + T.off;
+  double* Fout = A.Fout + T.off;
+  const int x = x0 + c;
+  const bool cell = (c < TX) && (x < Nx);
+  for (int k = tid; k < RW; k += NT) sm.src[k] = map_cell(x0 - HALO + k, Nx, T.bc);
+
+  if (T.collide) {
+    // A. moments of the stage input, velocity rows split over the NG groups
+    double m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+    if (cell) {
+      for (int j = g; j < Qxi; j += NG) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < Qp; ++i) {
+          const double f = __ldg(Fin + (size_t)(i * Qxi + j) * ld + x);
+          a = fma(f, tab[TAB_PBAR + i], a);
+          b = fma(f, tab[TAB_PBAR2 + i], b);
+        }
+        const double xi = tab[TAB_XI + j];
+        m0 += a;
+        m1 = fma(a, xi, m1);
+        m2 += b;
+        m3 = fma(b, xi, m3);
+        m4 = fma(b * xi, xi, m4);
+      }
+    }
+    sm.u.red[g][0][c] = m0;
+    sm.u.red[g][1][c] = m1;
+    sm.u.red[g][2][c] = m2;
+    sm.u.red[g][3][c] = m3;
+    sm.u.red[g][4][c] = m4;
+    __syncthreads();
+    // B. Landau frame (one thread per cell), then the equilibrium coefficients
+    double e = 1.0, beta = 0.0, n = 1.0, Tt = 1.0;
+    bool ok = false;
+    if (g == 0 && cell) {
+      double mom[5];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) mom[f] = (sm.u.red[0][f][c] + sm.u.red[1][f][c]) + (sm.u.red[2][f][c] + sm.u.red[3][f][c]);
+      ok = landau(mom, e, beta, n, Tt);
+      if (!ok) atomicOr(A.flag, 1);
+    }
+    __syncthreads();  // the moments are consumed; the union now holds the coefficient scratch
+    if (g == 0 && c < GW) {
+      sm.u.coef.cell[0][c] = n;
+      sm.u.coef.cell[1][c] = Tt;
+      sm.u.coef.cell[2][c] = beta;
+      sm.u.coef.ok[c] = ok ? 1 : 0;
+      const double r0 = ok ? T.inv_tau / sqrt(1.0 - beta * beta) : 0.0;
+      sm.rate[0][c] = r0;
+      sm.rate[1][c] = r0 * beta;
+    }
+    __syncthreads();
+    tile_coeffs<NPc, NVc>(tab, Qp, sm.u.coef, sm.B, A.flag);
+  }
+  __syncthreads();  // sm.src (and, with collisions, the coefficients) are ready
+
+  // C. advection + collision + Runge-Kutta combination, NG velocity rows at a time
+  const double dt = T.dt, inv_dx = 1.0 / T.dx, a = A.a, b = A.b;
+  int buf = 0;
+  for (int s0 = 0; s0 < Q; s0 += NG, buf ^= 1) {
+    const int s = s0 + g;
+    const bool rv = s < Q;
+    const int i = rv ? s / Qxi : 0, j = rv ? s - i * Qxi : 0;
+    double* row = sm.row[buf][g];
+    if (rv) {
+      const double* src = Fin + (size_t)s * ld;
+      for (int k = c; k < RW; k += GW) row[k] = __ldg(src + sm.src[k]);
+    }
+    __syncthreads();
+    const double xi = tab[TAB_XI + j];
+    double phi = 0.0;
+    if (rv) {
+      // interface c lies between cells x0 + c - 1 and x0 + c (row index c + 2 | c + 3)
+      if (xi > 0.0)
+        phi = weno5(row[c], row[c + 1], row[c + 2], row[c + 3], row[c + 4]);
+      else
+        phi = weno5(row[c + 5], row[c + 4], row[c + 3], row[c + 2], row[c + 1]);
+    }
+    sm.phi[buf][g][c] = phi;
+    __syncthreads();
+    if (rv && cell) {
+      const double F = row[c + 3];
+      double L = -(xi * inv_dx) * (sm.phi[buf][g][c + 1] - phi);
+      if (T.collide) {
+        const double* pw = tab + TAB_XI + Qxi + j * (NV_MAX + 1);
+        double feq = 0.0;
+#pragma unroll
+        for (int k = 0; k <= NVc; ++k) feq = fma(sm.B[i * (NV_MAX + 1) + k][c], pw[k], feq);
+        const double rate = fma(-sm.rate[1][c], xi, sm.rate[0][c]);
+        L = fma(-rate, F - feq, L);
+      }
+      double out = b * fma(dt, L, F);
+      if (a != 0.0) out = fma(a, Fn[(size_t)s * ld + x], out);
+      Fout[(size_t)s * ld + x] = out;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT) rlb_stage_kernel(StageArgs A) {
+  __shared__ StageSmem sm;
+  const int2 tl = A.tiles[blockIdx.x];
+  const TubeDev T = A.tubes[tl.x];
+  if (T.Np == 2 && T.Nv == 5)
+    stage_tile<2, 5>(A, T, tl.y, sm);
+  else
+    stage_tile<NP_MAX, NV_MAX>(A, T, tl.y, sm);
+}
+
+// --------------------------------------------------------------------------------------------------
+// Initial condition and fields
+// --------------------------------------------------------------------------------------------------
+
+struct InitArgs {
+  const TubeDev* tubes;
+  const int2* tiles;
+  double* F;
+  const double* tab;
+  const double* P;      // per-cell state (field layout) or NULL
+  const double* n;
+  const double* v;
+  const double* riem;   // per-tube (P_L, n_L, v_L, P_R, n_R, v_R) or NULL
+  int* flag;
+};
+
+struct InitSmem {
+  CoefSmem coef;
+  double B[NBC][GW];
+  int tie;
+};
+
+// Write F = F^eq of the cells' states (pass 0), or average the right-state equilibrium into the cells that
+// sit exactly on the membrane (pass 1).
+template <int NVc>
+__device__ void init_write(const TubeDev& T, const double* tab, const InitSmem& sm, double* F, int x0, bool pass1,
+                           bool tie) {
+  const int c = threadIdx.x % GW, g = threadIdx.x / GW, x = x0 + c;
+  if (c >= TX || x >= T.Nx || (pass1 && !tie)) return;
+  const int Q = T.Qp * T.Qxi;
+  for (int s = g; s < Q; s += NG) {
+    const int i = s / T.Qxi, j = s - i * T.Qxi;
+    const double* pw = tab + TAB_XI + T.Qxi + j * (NV_MAX + 1);
+    double f = 0.0;
+#pragma unroll
+    for (int k = 0; k <= NVc; ++k) f = fma(sm.B[i * (NV_MAX + 1) + k][c], pw[k], f);
+    double* dst = F + T.off + (size_t)s * T.ld + x;
+    *dst = pass1 ? 0.5 * (*dst + f) : f;
+  }
+}
+
+template <int NPc, int NVc>
+__device__ void init_tile(const InitArgs& A, const TubeDev& T, int x0, InitSmem& sm) {
+  const int c = threadIdx.x % GW, g = threadIdx.x / GW, x = x0 + c;
+  const double* tab = A.tab + T.tab;
+  const bool cell = c < TX && x < T.Nx;
+  // Riemann data: side of the membrane from the cell centre, evaluated without contraction so that it
+  // matches plain IEEE arithmetic; a centre exactly on x = 0 gets the mean of both equilibria.
+  const double xc = __dadd_rn(T.x_left, __dmul_rn((double)x + 0.5, T.dx));
+  const bool tie = cell && A.riem != nullptr && xc == 0.0;
+  if (threadIdx.x == 0) sm.tie = 0;
+  __syncthreads();
+  if (tie) sm.tie = 1;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (g == 0) {
+      double P = 1.0, n = 1.0, v = 0.0;
+      if (A.riem == nullptr) {
+        if (cell) {
+          const size_t k = (size_t)T.xoff + x;
+          P = A.P[k];
+          n = A.n[k];
+          v = A.v[k];
+        }
+      } else {
+        const double* st = A.riem + 6 * T.index + ((pass == 1 || xc > 0.0) ? 3 : 0);
+        P = st[0];
+        n = st[1];
+        v = st[2];
+      }
+      const bool ok = P > 0.0 && n > 0.0 && fabs(v) < 1.0;
+      if (cell && !ok) atomicOr(A.flag, 1);
+      sm.coef.cell[0][c] = n;
+      sm.coef.cell[1][c] = P / n;
+      sm.coef.cell[2][c] = v;
+      sm.coef.ok[c] = (cell && ok) ? 1 : 0;
+    }
+    __syncthreads();
+    if (pass == 1 && sm.tie == 0) break;  // uniform over the CTA
+    tile_coeffs<NPc, NVc>(tab, T.Qp, sm.coef, sm.B, A.flag);
+    init_write<NVc>(T, tab, sm, A.F, x0, pass == 1, tie);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(NT) rlb_init_kernel(InitArgs A) {
+  __shared__ InitSmem sm;
+  const int2 tl = A.tiles[blockIdx.x];
+  const TubeDev T = A.tubes[tl.x];
+  if (T.Np == 2 && T.Nv == 5)
+    init_tile<2, 5>(A, T, tl.y, sm);
+  else
+    init_tile<NP_MAX, NV_MAX>(A, T, tl.y, sm);
+}
+
+__global__ void __launch_bounds__(GW) rlb_fields_kernel(const TubeDev* tubes, const int2* tiles, const double* F,
+                                                         const double* tabs, double* out, long long nxtot,
+                                                         int* flag) {
+  const int2 tl = tiles[blockIdx.x];
+  const TubeDev T = tubes[tl.x];
+  const int c = threadIdx.x, x = tl.y + c;
+  if (c >= TX || x >= T.Nx) return;
+  const double* tab = tabs + T.tab;
+  const double* f = F + T.off + x;
+  double mom[5] = {0, 0, 0, 0, 0};
+  for (int j = 0; j < T.Qxi; ++j) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < T.Qp; ++i) {
+      const double v = f[(size_t)(i * T.Qxi + j) * T.ld];
+      a = fma(v, tab[TAB_PBAR + i], a);
+      b = fma(v, tab[TAB_PBAR2 + i], b);
+    }
+    const double xi = tab[TAB_XI + j];
+    mom[0] += a;
+    mom[1] = fma(a, xi, mom[1]);
+    mom[2] += b;
+    mom[3] = fma(b, xi, mom[3]);
+    mom[4] = fma(b * xi, xi, mom[4]);
+  }
+  double e, beta, n, Tt;
+  if (!landau(mom, e, beta, n, Tt)) atomicOr(flag, 1);
+  double* o = out + T.xoff + x;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) o[k * nxtot] = mom[k];
+  o[5 * nxtot] = e;
+  o[6 * nxtot] = beta;
+  o[7 * nxtot] = n;
+}
+
+// --------------------------------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------------------------------
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else if (prev == dev) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+rlb_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return RLB_OK;
+  return e == cudaErrorMemoryAllocation ? RLB_ENOMEM : RLB_ECUDA;
+}
+
+#define RLB_CUDA(call)                               \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_status(e_);   \
+  } while (0)
+
+std::mutex g_tables_mu;
+bool g_tables_ready[64] = {};
+
+// Fill the series tables of this device once (long double on the host).
+rlb_status ensure_series_tables(int dev) {
+  std::lock_guard<std::mutex> lk(g_tables_mu);
+  if (dev < 0 || dev >= 64) return RLB_EINVAL;
+  if (g_tables_ready[dev]) return RLB_OK;
+  std::vector<double> ic((size_t)(R_MAX + 1) * (NV_MAX + 1), 0.0), cb((size_t)(M_MAX + 1) * (R_MAX + 1), 0.0);
+  for (int k = 0; k <= NV_MAX; ++k) {
+    // I_{k,k} = 2^{k+1} (k!)^2 / (2k+1)!; I_{r+2,k}/I_{r,k} = (r+1)(r+2)((r+k)/2+1) / (((r-k)/2+1)(r+k+2)(r+k+3))
+    long double I = 2.0L;
+    for (int q = 1; q <= k; ++q) I *= 2.0L * q * q / ((2.0L * q) * (2.0L * q + 1.0L));
+    for (int r = k; r <= R_MAX; r += 2) {
+      ic[(size_t)r * (NV_MAX + 1) + k] = (double)((2.0L * k + 1.0L) / 2.0L * I);
+      const long double hp = (r + k) / 2, hm = (r - k) / 2;
+      I *= (r + 1.0L) * (r + 2.0L) * (hp + 1.0L) / ((hm + 1.0L) * (r + k + 2.0L) * (r + k + 3.0L));
+    }
+  }
+  for (int m = 1; m <= M_MAX; ++m) {
+    long double C = 1.0L;  // C(m - 1, 0)
+    for (int r = 0; r <= R_MAX; ++r) {
+      cb[(size_t)m * (R_MAX + 1) + r] = (double)C;
+      C = C * (m + r) / (r + 1.0L);  // C(m + r, r + 1)
+    }
+  }
+  RLB_CUDA(cudaMemcpyToSymbol(g_ic, ic.data(), ic.size() * sizeof(double)));
+  RLB_CUDA(cudaMemcpyToSymbol(g_cb, cb.data(), cb.size() * sizeof(double)));
+  g_tables_ready[dev] = true;
+  return RLB_OK;
+}
+
+}  // namespace
+
+struct rlb_ctx {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<rlb_tube> tubes;
+  std::vector<TubeDev> td;
+  int ntiles = 0;
+  long long state_elems = 0;  // padded doubles per buffer
+  long long packed = 0;       // sum Q Nx
+  long long nxtot = 0;
+  TubeDev* d_tubes = nullptr;
+  int2* d_tiles = nullptr;
+  double* d_tab = nullptr;
+  double *F = nullptr, *F1 = nullptr, *F2 = nullptr;
+  double* d_fields = nullptr;  // scratch for host-side moments
+  int* d_flag = nullptr;
+  int* h_flag = nullptr;       // pinned
+};
+
+namespace {
+
+void free_ctx(rlb_ctx* h) {
+  if (!h) return;
+  DeviceGuard gd(h->dev);
+  cudaFree(h->d_tubes);
+  cudaFree(h->d_tiles);
+  cudaFree(h->d_tab);
+  cudaFree(h->F);
+  cudaFree(h->F1);
+  cudaFree(h->F2);
+  cudaFree(h->d_fields);
+  cudaFree(h->d_flag);
+  cudaFreeHost(h->h_flag);
+  delete h;
+}
+
+rlb_status validate(const rlb_tube* t) {
+  if (t->Qp < 1 || t->Qp > QP_MAX || t->Np < 1 || t->Np >= t->Qp || t->Np > NP_MAX) return RLB_EINVAL;
+  if (t->Nv < 2 || t->Nv > NV_MAX || t->Qxi < 1 || t->Qxi > QXI_MAX || 2 * t->Qxi < t->Nv + 3) return RLB_EINVAL;
+  if (t->Nx < 1 || t->Nx > (1LL << 30) || (t->bc == RLB_BC_PERIODIC && t->Nx < 3)) return RLB_EINVAL;
+  if (t->bc != RLB_BC_OPEN && t->bc != RLB_BC_PERIODIC) return RLB_EINVAL;
+  if (!(t->dx > 0.0) || !std::isfinite(t->dx) || !(t->dt > 0.0) || !std::isfinite(t->dt)) return RLB_EINVAL;
+  if (std::isnan(t->tau) || t->reserved != 0) return RLB_EINVAL;
+  return RLB_OK;
+}
+
+rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const double* xleft, void* stream,
+                  rlb_ctx** hp) {
+  if (!out || !tubes || ntubes < 1) return RLB_EINVAL;
+  *out = nullptr;
+  for (int b = 0; b < ntubes; ++b) {
+    rlb_status st = validate(&tubes[b]);
+    if (st != RLB_OK) return st;
+  }
+  rlb_ctx* h = new (std::nothrow) rlb_ctx;
+  if (!h) return RLB_ENOMEM;
+  *hp = h;
+  RLB_CUDA(cudaGetDevice(&h->dev));
+  h->stream = (cudaStream_t)stream;
+  h->tubes.assign(tubes, tubes + ntubes);
+  // quadrature tables, one block per tube
+  std::vector<double> tab;
+  std::map<std::pair<int, int>, int> seen;  // one table block per (Qp, Np, Nv, Qxi)
+  h->td.resize(ntubes);
+  long long off = 0, xoff = 0;
+  for (int b = 0; b < ntubes; ++b) {
+    const rlb_tube& t = tubes[b];
+    TubeDev& d = h->td[b];
+    d.Qp = t.Qp;
+    d.Qxi = t.Qxi;
+    d.Np = t.Np;
+    d.Nv = t.Nv;
+    d.bc = t.bc;
+    d.collide = (t.tau > 0.0 && std::isfinite(t.tau)) ? 1 : 0;
+    d.Nx = (int)t.Nx;
+    d.ld = (int)((t.Nx + 31) / 32 * 32);
+    d.off = off;
+    d.xoff = xoff;
+    d.dx = t.dx;
+    d.dt = t.dt;
+    d.inv_tau = d.collide ? 1.0 / t.tau : 0.0;
+    d.x_left = xleft ? xleft[b] : 0.0;
+    d.index = b;
+    off += (long long)t.Qp * t.Qxi * d.ld;
+    xoff += t.Nx;
+    h->packed += (long long)t.Qp * t.Qxi * t.Nx;
+    auto key = std::make_pair(t.Qp * 1000 + t.Np * 100 + t.Nv, t.Qxi);
+    auto it = seen.find(key);
+    if (it != seen.end()) {
+      d.tab = it->second;
+      continue;
+    }
+    d.tab = (int)tab.size();
+    seen[key] = d.tab;
+    tab.resize(tab.size() + tab_size(t.Qxi), 0.0);
+    double* T = tab.data() + d.tab;
+    std::vector<double> pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
+    if (!rlbq::gauss_laguerre1(t.Qp, pb.data(), wp.data()) || !rlbq::gauss_legendre(t.Qxi, xi.data(), wxi.data()))
+      return RLB_EINVAL;
+    for (int i = 0; i < t.Qp; ++i) {
+      T[TAB_PBAR + i] = pb[i];
+      T[TAB_PBAR2 + i] = pb[i] * pb[i];
+      T[TAB_WP + i] = wp[i];
+      // K[i][q] = (-1)^q sum_{l=q}^{Np} C(l, q) L^(1)_l(pbar_i)
+      for (int q = 0; q <= t.Np; ++q) {
+        long double acc = 0.0L;
+        for (int l = q; l <= t.Np; ++l) {
+          long double C = 1.0L;
+          for (int u = 1; u <= q; ++u) C = C * (l - q + u) / u;
+          acc += C * rlbq::laguerre1(l, pb[i]);
+        }
+        T[TAB_K + i * (NP_MAX + 1) + q] = (double)((q % 2) ? -acc : acc);
+      }
+    }
+    for (int j = 0; j < t.Qxi; ++j) {
+      T[TAB_XI + j] = xi[j];
+      for (int k = 0; k <= NV_MAX; ++k)
+        T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
+    }
+  }
+  h->state_elems = off;
+  h->nxtot = xoff;
+  // tiles, most expensive tubes first
+  std::vector<int> order(ntubes);
+  for (int b = 0; b < ntubes; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+    return tubes[p].Qp * tubes[p].Qxi > tubes[q].Qp * tubes[q].Qxi;
+  });
+  std::vector<int2> tiles;
+  for (int b : order)
+    for (int x0 = 0; x0 < (int)tubes[b].Nx; x0 += TX) tiles.push_back(make_int2(b, x0));
+  h->ntiles = (int)tiles.size();
+  DeviceGuard gd(h->dev);
+  RLB_CUDA(cudaMalloc(&h->d_tubes, sizeof(TubeDev) * ntubes));
+  RLB_CUDA(cudaMalloc(&h->d_tiles, sizeof(int2) * tiles.size()));
+  RLB_CUDA(cudaMalloc(&h->d_tab, sizeof(double) * std::max<size_t>(tab.size(), 1)));
+  RLB_CUDA(cudaMalloc(&h->F, sizeof(double) * h->state_elems));
+  RLB_CUDA(cudaMalloc(&h->F1, sizeof(double) * h->state_elems));
+  RLB_CUDA(cudaMalloc(&h->F2, sizeof(double) * h->state_elems));
+  RLB_CUDA(cudaMalloc(&h->d_flag, sizeof(int)));
+  RLB_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
+  RLB_CUDA(cudaMemcpyAsync(h->d_tubes, h->td.data(), sizeof(TubeDev) * ntubes, cudaMemcpyHostToDevice, h->stream));
+  RLB_CUDA(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
+  RLB_CUDA(cudaMemcpyAsync(h->d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->F, 0, sizeof(double) * h->state_elems, h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->F1, 0, sizeof(double) * h->state_elems, h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->F2, 0, sizeof(double) * h->state_elems, h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+  rlb_status st = ensure_series_tables(h->dev);
+  if (st != RLB_OK) return st;
+  return RLB_OK;
+}
+
+rlb_status check_flag(rlb_ctx* h) {
+  RLB_CUDA(cudaMemcpyAsync(h->h_flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  RLB_CUDA(cudaStreamSynchronize(h->stream));
+  if (*h->h_flag) {
+    RLB_CUDA(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+    return RLB_ENONPHYS;
+  }
+  return RLB_OK;
+}
+
+rlb_status run_init(rlb_ctx* h, const double* P, const double* n, const double* v, int on_device,
+                    const double* riem_host) {
+  InitArgs A{};
+  A.tubes = h->d_tubes;
+  A.tiles = h->d_tiles;
+  A.F = h->F;
+  A.tab = h->d_tab;
+  A.flag = h->d_flag;
+  double* tmp = nullptr;
+  if (riem_host) {
+    RLB_CUDA(cudaMalloc(&tmp, sizeof(double) * 6 * h->tubes.size()));
+    RLB_CUDA(cudaMemcpyAsync(tmp, riem_host, sizeof(double) * 6 * h->tubes.size(), cudaMemcpyHostToDevice, h->stream));
+    A.riem = tmp;
+  } else if (on_device) {
+    A.P = P;
+    A.n = n;
+    A.v = v;
+  } else {
+    RLB_CUDA(cudaMalloc(&tmp, sizeof(double) * 3 * h->nxtot));
+    RLB_CUDA(cudaMemcpyAsync(tmp, P, sizeof(double) * h->nxtot, cudaMemcpyHostToDevice, h->stream));
+    RLB_CUDA(cudaMemcpyAsync(tmp + h->nxtot, n, sizeof(double) * h->nxtot, cudaMemcpyHostToDevice, h->stream));
+    RLB_CUDA(cudaMemcpyAsync(tmp + 2 * h->nxtot, v, sizeof(double) * h->nxtot, cudaMemcpyHostToDevice, h->stream));
+    A.P = tmp;
+    A.n = tmp + h->nxtot;
+    A.v = tmp + 2 * h->nxtot;
+  }
+  rlb_init_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
+  cudaError_t e = cudaGetLastError();
+  rlb_status st = check_flag(h);  // also waits for the copies out of the caller's buffers
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (st == RLB_ENONPHYS) return RLB_EINVAL;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+rlb_status rlb_init(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const double* P, const double* n,
+                    const double* v, int32_t ic_on_device, void* stream) {
+  if (!P || !n || !v) return RLB_EINVAL;
+  rlb_ctx* h = nullptr;
+  rlb_status st = create(out, tubes, ntubes, nullptr, stream, &h);
+  if (st == RLB_OK) {
+    DeviceGuard gd(h->dev);
+    st = run_init(h, P, n, v, ic_on_device, nullptr);
+  }
+  if (st != RLB_OK) {
+    free_ctx(h);
+    return st;
+  }
+  *out = h;
+  return RLB_OK;
+}
+
+rlb_status rlb_init_riemann(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const double* states,
+                            const double* x_left, void* stream) {
+  if (!states || !x_left) return RLB_EINVAL;
+  for (int b = 0; b < ntubes; ++b)
+    if (!(states[6 * b] > 0) || !(states[6 * b + 1] > 0) || !(states[6 * b + 3] > 0) || !(states[6 * b + 4] > 0) ||
+        !(std::fabs(states[6 * b + 2]) < 1) || !(std::fabs(states[6 * b + 5]) < 1) || !std::isfinite(x_left[b]))
+      return RLB_EINVAL;
+  rlb_ctx* h = nullptr;
+  rlb_status st = create(out, tubes, ntubes, x_left, stream, &h);
+  if (st == RLB_OK) {
+    DeviceGuard gd(h->dev);
+    st = run_init(h, nullptr, nullptr, nullptr, 0, states);
+  }
+  if (st != RLB_OK) {
+    free_ctx(h);
+    return st;
+  }
+  *out = h;
+  return RLB_OK;
+}
+
+rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
+  if (!h || nsteps < 0) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  StageArgs A{};
+  A.tubes = h->d_tubes;
+  A.tiles = h->d_tiles;
+  A.tab = h->d_tab;
+  A.flag = h->d_flag;
+  A.Fn = h->F;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    A.Fin = h->F;
+    A.Fout = h->F1;
+    A.a = 0.0;
+    A.b = 1.0;
+    rlb_stage_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
+    A.Fin = h->F1;
+    A.Fout = h->F2;
+    A.a = 0.75;
+    A.b = 0.25;
+    rlb_stage_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
+    A.Fin = h->F2;
+    A.Fout = h->F;
+    A.a = 1.0 / 3.0;
+    A.b = 2.0 / 3.0;
+    rlb_stage_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+rlb_status rlb_moments(rlb_handle h, double* out, int32_t out_on_device) {
+  if (!h || !out) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  double* dst = out;
+  if (!out_on_device) {
+    if (!h->d_fields) RLB_CUDA(cudaMalloc(&h->d_fields, sizeof(double) * RLB_NFIELDS * h->nxtot));
+    dst = h->d_fields;
+  }
+  rlb_fields_kernel<<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab, dst, h->nxtot,
+                                                      h->d_flag);
+  RLB_CUDA(cudaGetLastError());
+  if (!out_on_device)
+    RLB_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * RLB_NFIELDS * h->nxtot, cudaMemcpyDeviceToHost, h->stream));
+  return check_flag(h);
+}
+
+static rlb_status copy_state(rlb_handle h, double* host_or_dev, const double* src_const, int32_t on_device,
+                             bool to_handle) {
+  DeviceGuard gd(h->dev);
+  long long p = 0;
+  for (size_t b = 0; b < h->tubes.size(); ++b) {
+    const TubeDev& d = h->td[b];
+    const size_t rows = (size_t)d.Qp * d.Qxi;
+    cudaMemcpyKind kind;
+    if (to_handle)
+      kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    else
+      kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (to_handle)
+      RLB_CUDA(cudaMemcpy2DAsync(h->F + d.off, sizeof(double) * d.ld, src_const + p, sizeof(double) * d.Nx,
+                                 sizeof(double) * d.Nx, rows, kind, h->stream));
+    else
+      RLB_CUDA(cudaMemcpy2DAsync(host_or_dev + p, sizeof(double) * d.Nx, h->F + d.off, sizeof(double) * d.ld,
+                                 sizeof(double) * d.Nx, rows, kind, h->stream));
+    p += (long long)rows * d.Nx;
+  }
+  if (!on_device || !to_handle) return check_flag(h);
+  return RLB_OK;
+}
+
+rlb_status rlb_get_state(rlb_handle h, double* F, int32_t on_device) {
+  if (!h || !F) return RLB_EINVAL;
+  return copy_state(h, F, nullptr, on_device, false);
+}
+
+rlb_status rlb_set_state(rlb_handle h, const double* F, int32_t on_device) {
+  if (!h || !F) return RLB_EINVAL;
+  return copy_state(h, nullptr, F, on_device, true);
+}
+
+rlb_status rlb_sync(rlb_handle h) {
+  if (!h) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  return check_flag(h);
+}
+
+rlb_status rlb_destroy(rlb_handle h) {
+  if (!h) return RLB_OK;
+  {
+    DeviceGuard gd(h->dev);
+    cudaStreamSynchronize(h->stream);
+  }
+  free_ctx(h);
+  return RLB_OK;
+}
+
+int64_t rlb_state_size(rlb_handle h) { return h ? h->packed : -1; }
+
+const char* rlb_error_string(rlb_status s) {
+  switch (s) {
+    case RLB_OK: return "RLB_OK";
+    case RLB_EINVAL: return "RLB_EINVAL: invalid argument";
+    case RLB_ENOMEM: return "RLB_ENOMEM: out of memory";
+    case RLB_ECUDA: return "RLB_ECUDA: CUDA runtime error";
+    case RLB_ENONPHYS: return "RLB_ENONPHYS: non-physical state (e <= 0, |v| >= 1, n <= 0 or NaN)";
+  }
+  return "unknown rlb_status";
+}
+
+double rlb_suggest_dt(double dx, double tau, double cfl) {
+  double dt = cfl * dx;
+  if (tau > 0.0 && std::isfinite(tau)) dt = std::min(dt, 1.25 * tau);
+  return dt;
+}
+
+rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double* pbar, double* wp, double* xi, double* wxi) {
+  if (Qp < 1 || Qp > 64 || Qxi < 1 || Qxi > QXI_MAX || !pbar || !wp || !xi || !wxi) return RLB_EINVAL;
+  if (!rlbq::gauss_laguerre1(Qp, pbar, wp) || !rlbq::gauss_legendre(Qxi, xi, wxi)) return RLB_EINVAL;
+  return RLB_OK;
+}
+
+}  // extern "C"

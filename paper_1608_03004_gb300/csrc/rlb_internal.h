@@ -1,0 +1,54 @@
+// Internal declarations of the CUDA library (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+
+namespace rlbq {
+bool gauss_legendre(int n, double* x, double* w);
+bool gauss_laguerre1(int n, double* x, double* w);
+double laguerre1(int l, double x);  // L^(1)_l(x)
+double legendre(int k, double x);   // P_k(x)
+}  // namespace rlbq
+
+namespace rlb {
+
+// Compile-time maxima of the orders the kernels support.
+constexpr int QP_MAX = 4;
+constexpr int NP_MAX = 3;             // Np < Qp <= QP_MAX
+constexpr int NV_MAX = 8;
+constexpr int M_MAX = NP_MAX + 2;     // powers (1 - beta xi)^-m, m = 2 .. Np + 2
+constexpr int QXI_MAX = 1024;
+constexpr int R_MAX = 16383;          // longest series for the Legendre coefficients (|v| up to ~0.995)
+
+// Per-tube description as the kernels see it.
+struct TubeDev {
+  int Qp, Qxi, Np, Nv;
+  int bc;       // 0 open, 1 periodic
+  int collide;  // 0: ballistic
+  int Nx;       // cells
+  int ld;       // row stride in doubles (padded)
+  long long off;   // offset of row 0 of this tube in the state buffers
+  long long xoff;  // offset of this tube's cells in the field layout
+  double dx, dt, inv_tau;
+  double x_left;
+  int tab;      // offset of this tube's tables in the table buffer
+  int index;    // position of the tube in the caller's list
+};
+
+// Layout of one tube's tables (doubles, starting at TubeDev::tab):
+//   [0, QP_MAX)                 pbar_i
+//   [QP_MAX, 2 QP_MAX)          pbar_i^2
+//   [2 QP_MAX, 3 QP_MAX)        w^p_i
+//   [3 QP_MAX, 3 QP_MAX + QP_MAX (NP_MAX+1))   K[i][q] = (-1)^q sum_{l=q}^{Np} C(l,q) L^(1)_l(pbar_i)
+//                                               at [i (NP_MAX+1) + q]: the radial factor multiplying
+//                                               s^(q+2) hhat_{q+2,k} in the truncated equilibrium
+//   then xi_j (Qxi), then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k] (Qxi (NV_MAX+1)), zero for k > Nv
+constexpr int TAB_PBAR = 0;
+constexpr int TAB_PBAR2 = QP_MAX;
+constexpr int TAB_WP = 2 * QP_MAX;
+constexpr int TAB_K = 3 * QP_MAX;
+constexpr int TAB_XI = TAB_K + QP_MAX * (NP_MAX + 1);
+inline int tab_pw(int Qxi) { return TAB_XI + Qxi; }
+inline int tab_size(int Qxi) { return TAB_XI + Qxi + Qxi * (NV_MAX + 1); }
+
+}  // namespace rlb

@@ -1,0 +1,138 @@
+"""Seeded synthetic workloads (tube descriptions and initial states). No step of the method lives here.
+
+Each workload is a list of ``TubeSpec``: grid, quadrature orders, relaxation time, time step and an initial
+condition, either Riemann data (left/right states of Eq. (condinit), section "Riemann problem") or per-cell
+(P, n, v) arrays. Tests feed the same specs to the CUDA path and to the oracle; the benchmark times them.
+
+Workloads (sizes as stated):
+  * ``sod_small``: the paper's Sod tube (P, n, v) = (1, 1, 0) | (0.1, 0.125, 0) on x in [-0.5, 0.5],
+    Nx = 400, Qp = 3, Qxi = 8 (24 velocities), tau = 1e-3, CFL 0.5 (dt = 1.25e-3, 320 steps to t = 0.4).
+  * ``sod_sweep``: the relaxation-time sweep, Nx = 4096, tau in {1e-4, 1e-3, 1e-2, 1e-1, 1, 10, inf} x
+    Qxi in {8, 32, 128, 200}, Qp = 3: 28 tubes, 31.65 M velocity nodes; dt = min(0.5 dx, 1.25 tau).
+  * ``batched_tubes``: 256 tubes, seed 160803004: Nx ~ U[1024, 16384], log10 tau ~ U[-4, 1],
+    Qxi in {8, 16, 32, 64}, P_L ~ U[0.5, 2], P_R = P_L U(0.01, 0.5), n_L = P_L, n_R = P_R / 0.8 (the paper
+    is silent on n; this keeps its T_L = 1, T_R = 0.8 and reproduces (1, 0.125) at P = (1, 0.1)).
+  * ``gaussian_bumps``: Nx = 2048, Qxi = 32, per-cell pressure 1 + sum of seed-fixed Gaussian bumps of
+    relative amplitude 0.05, n = P, v = 0.
+  * ``stress``: one Sod tube, Nx = 1,048,576, Qxi = 128 (384 velocities), tau = 1e-2.
+  * ``random_smooth``: seeded smooth periodic (P, n, v) profiles for parity tests.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+SOD_LEFT = (1.0, 1.0, 0.0)
+SOD_RIGHT = (0.1, 0.125, 0.0)
+BC_OPEN, BC_PERIODIC = 0, 1
+SWEEP_TAUS = (1e-4, 1e-3, 1e-2, 1e-1, 1.0, 10.0, math.inf)
+SWEEP_QXI = (8, 32, 128, 200)
+BATCH_SEED = 160803004
+
+
+@dataclasses.dataclass
+class TubeSpec:
+    Nx: int
+    Qxi: int
+    tau: float
+    dt: float
+    dx: float
+    Qp: int = 3
+    Np: int = 2
+    Nv: int = 5
+    bc: int = BC_OPEN
+    x_left: float = -0.5
+    left: Optional[Sequence[float]] = SOD_LEFT    # Riemann data ...
+    right: Optional[Sequence[float]] = SOD_RIGHT
+    P: Optional[np.ndarray] = None                # ... or per-cell (P, n, v)
+    n: Optional[np.ndarray] = None
+    v: Optional[np.ndarray] = None
+
+    @property
+    def Q(self) -> int:
+        return self.Qp * self.Qxi
+
+    @property
+    def riemann(self) -> bool:
+        return self.P is None
+
+
+def cfl_dt(dx: float, tau: float, cfl: float = 0.5) -> float:
+    """Time step rule of the workloads: min(cfl dx, 1.25 tau) (1.25 tau keeps SSP-RK3 stable for |v| <= 0.6)."""
+    dt = cfl * dx
+    if tau is not None and math.isfinite(tau) and tau > 0:
+        dt = min(dt, 1.25 * tau)
+    return dt
+
+
+def sod_tube(Nx: int, Qxi: int, tau: float, Qp: int = 3, Np: int = 2, Nv: int = 5, cfl: float = 0.5,
+             bc: int = BC_OPEN, x_left: float = -0.5, length: float = 1.0, left=SOD_LEFT,
+             right=SOD_RIGHT) -> TubeSpec:
+    dx = length / Nx
+    return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau, cfl), dx=dx, Qp=Qp, Np=Np, Nv=Nv, bc=bc,
+                    x_left=x_left, left=tuple(left), right=tuple(right))
+
+
+def sod_small() -> List[TubeSpec]:
+    return [sod_tube(400, 8, 1e-3)]
+
+
+def sod_sweep(Nx: int = 4096, taus=SWEEP_TAUS, qxis=SWEEP_QXI) -> List[TubeSpec]:
+    return [sod_tube(Nx, q, t) for t in taus for q in qxis]
+
+
+def batched_tubes(ntubes: int = 256, seed: int = BATCH_SEED) -> List[TubeSpec]:
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(ntubes):
+        Nx = int(rng.integers(1024, 16384, endpoint=True))
+        tau = float(10.0 ** rng.uniform(-4, 1))
+        Qxi = int(rng.choice([8, 16, 32, 64]))
+        PL = float(rng.uniform(0.5, 2.0))
+        PR = PL * float(rng.uniform(0.01, 0.5))
+        out.append(sod_tube(Nx, Qxi, tau, left=(PL, PL, 0.0), right=(PR, PR / 0.8, 0.0)))
+    return out
+
+
+def gaussian_bumps(Nx: int = 2048, Qxi: int = 32, tau: float = 0.05, amplitude: float = 0.05, seed: int = 4,
+                   nbumps: int = 5) -> TubeSpec:
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / Nx
+    x = -0.5 + (np.arange(Nx) + 0.5) * dx
+    P = np.ones(Nx)
+    for _ in range(nbumps):
+        c, w = rng.uniform(-0.3, 0.3), rng.uniform(0.02, 0.08)
+        P += amplitude * rng.uniform(0.5, 1.0) * np.exp(-0.5 * ((x - c) / w) ** 2)
+    return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau), dx=dx, P=P, n=P.copy(), v=np.zeros(Nx))
+
+
+def stress(Nx: int = 1 << 20, Qxi: int = 128, tau: float = 1e-2) -> TubeSpec:
+    return sod_tube(Nx, Qxi, tau)
+
+
+def random_smooth(Nx: int, Qxi: int, tau: float, seed: int, bc: int = BC_PERIODIC, vmax: float = 0.5,
+                  Qp: int = 3, Np: int = 2, Nv: int = 5, cfl: float = 0.5) -> TubeSpec:
+    """Smooth random periodic profiles: P in [0.3, 1.7], n in [0.3, 1.7], |v| <= vmax (few Fourier modes)."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / Nx
+    x = (np.arange(Nx) + 0.5) * dx
+
+    def field(amp):
+        f = np.zeros(Nx)
+        for k in range(1, 4):
+            f += rng.uniform(-1, 1) * np.sin(2 * np.pi * k * x + rng.uniform(0, 2 * np.pi)) / k
+        return amp * f / max(np.max(np.abs(f)), 1e-12)
+
+    P = 1.0 + field(0.7)
+    n = 1.0 + field(0.7)
+    v = field(vmax)
+    return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau, cfl), dx=dx, Qp=Qp, Np=Np, Nv=Nv, bc=bc,
+                    x_left=0.0, P=P, n=n, v=v)
+
+
+def total_nodes(specs: Sequence[TubeSpec]) -> int:
+    """Velocity nodes per step, sum of Nx * Q."""
+    return int(sum(s.Nx * s.Q for s in specs))

@@ -1,0 +1,96 @@
+"""Glue between the seeded workload specs, the CUDA path (through the C ABI) and the oracle.
+
+Parity rule used by every GPU test: for each row r (one velocity of F, or one field) of one tube,
+    max_x |gpu - oracle| <= rtol * max_x |oracle|,   rtol = 1e-12 (FP64),
+and, for the strictly positive fields (N^0, T^00, T^xx, e, n), also pointwise |gpu - oracle| <= 10 rtol |oracle|.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Sequence
+
+import numpy as np
+
+import oracle
+from paper_1608_03004_gb300 import binding as rb
+from paper_1608_03004_gb300.workloads import TubeSpec
+
+RTOL = 1e-12
+POSITIVE_FIELDS = (0, 2, 4, 5, 7)
+
+
+def to_tube(s: TubeSpec) -> rb.Tube:
+    tau = s.tau if (s.tau is not None and math.isfinite(s.tau) and s.tau > 0) else math.inf
+    return rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, tau, s.bc, 0)
+
+
+def to_params(s: TubeSpec) -> oracle.Params:
+    tau = s.tau if (s.tau is not None and math.isfinite(s.tau) and s.tau > 0) else 0.0
+    return oracle.Params(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, tau, s.bc)
+
+
+def gpu_init(specs: Sequence[TubeSpec]) -> rb.Handle:
+    tubes = [to_tube(s) for s in specs]
+    if all(s.riemann for s in specs):
+        states = np.array([list(s.left) + list(s.right) for s in specs], dtype=np.float64)
+        xl = np.array([s.x_left for s in specs], dtype=np.float64)
+        return rb.rlb_init_riemann(tubes, states, xl)
+    assert not any(s.riemann for s in specs), "one handle takes either Riemann data or per-cell states"
+    P = np.concatenate([s.P for s in specs])
+    n = np.concatenate([s.n for s in specs])
+    v = np.concatenate([s.v for s in specs])
+    return rb.rlb_init(tubes, P, n, v)
+
+
+def oracle_init(s: TubeSpec) -> np.ndarray:
+    p = to_params(s)
+    if s.riemann:
+        return oracle.init_riemann(p, left=s.left, right=s.right, xleft=s.x_left)
+    return oracle.init(p, s.P, s.n, s.v)
+
+
+def split_state(specs: Sequence[TubeSpec], flat: np.ndarray) -> List[np.ndarray]:
+    out, p = [], 0
+    for s in specs:
+        k = s.Q * s.Nx
+        out.append(flat[p:p + k].reshape(s.Q, s.Nx))
+        p += k
+    return out
+
+
+def split_fields(specs: Sequence[TubeSpec], fields: np.ndarray) -> List[np.ndarray]:
+    out, p = [], 0
+    for s in specs:
+        out.append(fields[:, p:p + s.Nx])
+        p += s.Nx
+    return out
+
+
+def row_errors(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """Normwise relative error of each row."""
+    scale = np.max(np.abs(ref), axis=1)
+    err = np.max(np.abs(gpu - ref), axis=1)
+    return np.where(scale > 0, err / np.where(scale > 0, scale, 1.0), err)
+
+
+def assert_state_parity(gpu: np.ndarray, ref: np.ndarray, rtol: float = RTOL, what: str = "F"):
+    e = row_errors(gpu, ref)
+    assert np.all(np.isfinite(gpu)), f"{what}: non-finite values"
+    assert e.max() <= rtol, f"{what}: worst row error {e.max():.3e} at row {int(e.argmax())}"
+    return float(e.max())
+
+
+def assert_field_parity(gpu: np.ndarray, ref: np.ndarray, rtol: float = RTOL, what: str = "fields"):
+    e = row_errors(gpu, ref)
+    assert np.all(np.isfinite(gpu)), f"{what}: non-finite values"
+    assert e.max() <= rtol, f"{what}: worst field error {e.max():.3e} in field {rb.FIELDS[int(e.argmax())]}"
+    for f in POSITIVE_FIELDS:
+        pr = np.max(np.abs(gpu[f] - ref[f]) / np.abs(ref[f]))
+        assert pr <= 10 * rtol, f"{what}: pointwise error {pr:.3e} in {rb.FIELDS[f]}"
+    return float(e.max())
+
+
+def oracle_run(s: TubeSpec, nsteps: int):
+    p = to_params(s)
+    F = oracle.step(p, oracle_init(s), nsteps) if nsteps else oracle_init(s)
+    return F, oracle.fields(p, F)

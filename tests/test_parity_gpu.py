@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA time step (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerance: 1e-12 relative (row-normwise for F and every field; pointwise for the positive fields), the
+FP64 parity bar. Cases: the paper's Sod tube at Nx = 400 over the whole run to t = 0.4, ragged and tiny
+grids around the 63-cell tile, odd Qxi (a xi = 0 node), a cell centre on the membrane, periodic grids,
+moving smooth states, the ballistic regime, high and low quadrature / truncation orders, mixed batches,
+and the full relaxation-time sweep (Nx = 4096, 28 tubes) in the launch configuration of the benchmark,
+checked on one-step windows the oracle recomputes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import harness as H
+import oracle
+from paper_1608_03004_gb300 import binding as rb
+from paper_1608_03004_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(specs, nsteps):
+    with H.gpu_init(specs) as h:
+        if nsteps:
+            rb.rlb_step(h, nsteps)
+        F = rb.rlb_get_state(h)
+        fields = rb.rlb_moments(h)
+    return H.split_state(specs, F), H.split_fields(specs, fields)
+
+
+def check(specs, nsteps, rtol=H.RTOL):
+    Fg, fg = run_gpu(specs, nsteps)
+    worst = 0.0
+    for s, F, f in zip(specs, Fg, fg):
+        Fr, fr = H.oracle_run(s, nsteps)
+        worst = max(worst, H.assert_state_parity(F, Fr, rtol, f"F Nx={s.Nx} Qxi={s.Qxi} tau={s.tau}"))
+        worst = max(worst, H.assert_field_parity(f, fr, rtol, f"fields Nx={s.Nx} Qxi={s.Qxi} tau={s.tau}"))
+    return worst
+
+
+@pytest.mark.parametrize("nsteps", [0, 1, 10])
+def test_sod_small_early_steps(nsteps):
+    check(W.sod_small(), nsteps)
+
+
+def test_sod_small_full_run_to_t04():
+    s = W.sod_small()[0]
+    nsteps = int(round(0.4 / s.dt))
+    assert nsteps == 320
+    check([s], nsteps)
+
+
+@pytest.mark.parametrize("Nx", [1, 2, 7, 62, 63, 64, 126, 127, 129, 200])
+def test_ragged_grids_open(Nx):
+    check([W.sod_tube(Nx, 8, 1e-3)], 5)
+
+
+@pytest.mark.parametrize("Nx", [3, 5, 64, 127])
+def test_ragged_grids_periodic(Nx):
+    check([W.random_smooth(Nx, 8, 1e-2, seed=Nx)], 5)
+
+
+@pytest.mark.parametrize("Qxi", [4, 5, 7, 16, 33])
+def test_quadrature_orders(Qxi):
+    check([W.sod_tube(96, Qxi, 2e-3)], 8)
+
+
+@pytest.mark.parametrize("Qxi", [128, 200])
+def test_high_quadrature_orders(Qxi):
+    check([W.sod_tube(64, Qxi, 1e-2)], 4)
+
+
+def test_membrane_on_a_cell_centre():
+    s = W.sod_tube(65, 8, 1e-3)
+    xc = s.x_left + (32 + 0.5) * s.dx
+    assert xc == 0.0  # this grid puts a centre exactly on the membrane
+    check([s], 3)
+
+
+@pytest.mark.parametrize("Qp,Np,Nv,Qxi", [(2, 1, 2, 3), (3, 1, 5, 4), (3, 2, 3, 4), (4, 3, 8, 6), (4, 2, 5, 8)])
+def test_truncation_orders(Qp, Np, Nv, Qxi):
+    check([W.random_smooth(80, Qxi, 5e-3, seed=Qp * 100 + Nv, Qp=Qp, Np=Np, Nv=Nv, bc=W.BC_OPEN)], 6)
+
+
+@pytest.mark.parametrize("vmax", [0.3, 0.7])
+def test_moving_smooth_states(vmax):
+    check([W.random_smooth(150, 16, 2e-2, seed=int(vmax * 10), vmax=vmax)], 12)
+
+
+def test_ballistic():
+    check([W.sod_tube(300, 16, math.inf)], 40)
+
+
+def test_mixed_batch_in_one_handle():
+    specs = [W.random_smooth(70, 8, 1e-2, seed=1), W.random_smooth(130, 32, math.inf, seed=2),
+             W.random_smooth(64, 5, 3e-3, seed=3, bc=W.BC_OPEN), W.random_smooth(9, 16, 1e-1, seed=4)]
+    check(specs, 6)
+
+
+def test_riemann_batch_in_one_handle():
+    specs = [W.sod_tube(100, 8, 1e-3), W.sod_tube(57, 16, math.inf),
+             W.sod_tube(128, 4, 1e-2, left=(2.0, 2.0, 0.1), right=(0.05, 0.0625, -0.2))]
+    check(specs, 6)
+
+
+def test_sweep_full_size_windows():
+    """The 28-tube relaxation-time sweep at Nx = 4096 in one handle (the benchmark's launch configuration):
+    after 40 GPU steps, one more GPU step is compared, at sampled cells, with one oracle step on windows of
+    +-9 cells taken from the GPU state (a step reaches 3 cells per stage, so window edges cannot affect the
+    window centre); fields are compared at the same cells."""
+    specs = W.sod_sweep()
+    rng = np.random.default_rng(7)
+    with H.gpu_init(specs) as h:
+        rb.rlb_step(h, 40)
+        F0 = H.split_state(specs, rb.rlb_get_state(h))
+        rb.rlb_step(h, 1)
+        F1 = H.split_state(specs, rb.rlb_get_state(h))
+        f1 = H.split_fields(specs, rb.rlb_moments(h))
+    for s, A, B, fB in zip(specs, F0, F1, f1):
+        Nx = s.Nx
+        # around the waves at t = 41 dt (x = 0 +- t) and both ends, plus random cells
+        t = 41 * s.dt
+        xs = [0, Nx - 1, Nx // 2, Nx // 2 - 1, int((0.5 + t) * Nx), int((0.5 - 0.58 * t) * Nx)]
+        xs += list(rng.integers(0, Nx, 3))
+        for x in xs:
+            lo, hi = max(0, x - 9), min(Nx, x + 10)
+            sub = W.TubeSpec(Nx=hi - lo, Qxi=s.Qxi, tau=s.tau, dt=s.dt, dx=s.dx, Qp=s.Qp, Np=s.Np, Nv=s.Nv, bc=s.bc)
+            p = H.to_params(sub)
+            ref = oracle.step(p, np.ascontiguousarray(A[:, lo:hi]), 1)
+            k = x - lo
+            got = B[:, x]
+            scale = np.max(np.abs(B), axis=1)
+            err = np.max(np.abs(got - ref[:, k]) / scale)
+            assert err <= H.RTOL, (s.Qxi, s.tau, x, err)
+            fr = oracle.fields(p, ref)[:, k]
+            fscale = np.maximum(np.max(np.abs(fB), axis=1), 1e-300)
+            ferr = np.max(np.abs(fB[:, x] - fr) / fscale)
+            assert ferr <= H.RTOL, (s.Qxi, s.tau, x, ferr)
+
+
+def test_state_round_trip_and_device_paths():
+    torch = pytest.importorskip("torch")
+    specs = [W.sod_tube(100, 8, 1e-3), W.sod_tube(37, 4, 1e-2)]
+    with H.gpu_init(specs) as h:
+        rb.rlb_step(h, 3)
+        host = rb.rlb_get_state(h)
+        dev = torch.empty(h.state_size, dtype=torch.float64, device="cuda")
+        rb.rlb_get_state(h, dev)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(dev.cpu().numpy(), host)
+        fh = rb.rlb_moments(h)
+        fd = torch.empty((8, h.nx_total), dtype=torch.float64, device="cuda")
+        rb.rlb_moments(h, fd)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(fd.cpu().numpy(), fh)
+        # checkpoint, advance, restore, advance again: identical results
+        rb.rlb_step(h, 5)
+        after = rb.rlb_get_state(h)
+        rb.rlb_set_state(h, dev)
+        rb.rlb_step(h, 5)
+        np.testing.assert_array_equal(rb.rlb_get_state(h), after)
+        rb.rlb_set_state(h, host)
+        rb.rlb_step(h, 5)
+        np.testing.assert_array_equal(rb.rlb_get_state(h), after)
+
+
+def test_device_initial_condition_matches_host():
+    torch = pytest.importorskip("torch")
+    s = W.random_smooth(90, 8, 1e-2, seed=11)
+    with H.gpu_init([s]) as h:
+        a = rb.rlb_get_state(h)
+    t = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in (s.P, s.n, s.v)]
+    with rb.rlb_init([H.to_tube(s)], *t) as h2:
+        b = rb.rlb_get_state(h2)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_nonphysical_state_is_reported():
+    s = W.sod_tube(64, 8, 1e-3)
+    with H.gpu_init([s]) as h:
+        F = rb.rlb_get_state(h)
+        rb.rlb_set_state(h, -F)  # negative populations: e < 0
+        rb.rlb_step(h, 1)
+        with pytest.raises(rb.RlbError) as ei:
+            rb.rlb_sync(h)
+        assert ei.value.status == rb.ENONPHYS
+        rb.rlb_sync(h)  # the flag is cleared once reported
+
+
+def test_bad_initial_state_rejected():
+    s = W.random_smooth(32, 8, 1e-2, seed=5)
+    s.P = s.P.copy()
+    s.P[3] = -1.0
+    with pytest.raises(rb.RlbError) as ei:
+        H.gpu_init([s])
+    assert ei.value.status == rb.EINVAL
