@@ -86,9 +86,10 @@ __device__ __forceinline__ bool landau(const double mom[5], double& e, double& b
 // WENO5 interface value from five samples ordered along the wind (v2 is the upwind cell next to the
 // interface). Same scheme as Jiang & Shu: candidates (2,-7,11)/6, (-1,5,2)/6, (2,5,-1)/6, smoothness
 // indicators with weights 13/12 and 1/4, linear weights (1, 6, 3)/10, alpha_k = d_k/(eps + beta_k)^2.
-// Written on the first differences d_l: 3 beta_k is the quadratic form (4x^2 - 11xy + 10y^2,
-// 4x^2 - 5xy + 4y^2, 10x^2 - 11xy + 4y^2) of adjacent differences, and the common factors of the alphas
-// are cancelled so that only one division remains.
+// Written on the first differences d_l = v_l - v_{l-1}: 3 beta_k is the quadratic form (4x^2 - 11xy + 10y^2,
+// 4x^2 - 5xy + 4y^2, 10x^2 - 11xy + 4y^2) of adjacent differences, the candidates are
+// v2 + (5 d2 - 2 d1)/6, v2 + (d2 + 2 d3)/6, v2 + (4 d3 - d4)/6, and the common factors of the alphas are
+// cancelled so that only one division remains.
 __device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4) {
   const double d1 = v1 - v0, d2 = v2 - v1, d3 = v3 - v2, d4 = v4 - v3;
   const double q1 = d1 * d1, q2 = d2 * d2, q3 = d3 * d3, q4 = d4 * d4;
@@ -99,7 +100,7 @@ __device__ __forceinline__ double weno5(double v0, double v1, double v2, double 
   const double u2 = fma(10.0, q3, fma(-11.0, p34, fma(4.0, q4, E)));
   const double s0 = u0 * u0, s1 = u1 * u1, s2 = u2 * u2;
   const double a0 = s1 * s2, a1 = 6.0 * (s0 * s2), a2 = 3.0 * (s0 * s1);
-  const double r0 = fma(5.0, d2, -2.0 * d1), r1 = fma(2.0, d3, d2), r2 = fma(5.0, d3, -d4);
+  const double r0 = fma(5.0, d2, -2.0 * d1), r1 = fma(2.0, d3, d2), r2 = fma(4.0, d3, -d4);
   const double num = fma(a0, r0, fma(a1, r1, a2 * r2));
   return v2 + num / (6.0 * (a0 + a1 + a2));
 }
