@@ -27,8 +27,10 @@
  *    stream. Errors are returned, never aborted on. A cell that reaches a non-physical state (e <= 0,
  *    |v| >= 1, n <= 0 or NaN) sets a sticky device flag; the next call that synchronises (rlb_moments,
  *    rlb_get_state, rlb_sync) returns RLB_ENONPHYS.
- *  - Limits: 1 <= Np < Qp <= 4, 2 <= Nv <= 8, 2*Qxi >= Nv + 3 (exact recovery of T^{mu nu}, Eq. (mom_feq)),
- *    Qxi <= 1024, Nx >= 1 (periodic: Nx >= 3), dx > 0, dt > 0.
+ *  - Limits: 2 <= Np < Qp <= 4 and 2 <= Nv <= 8 with 2*Qxi >= Nv + 3: T^{mu nu} is of second order in pbar
+ *    and in xi, so Eq. (mom_feq) recovers it exactly only with Np >= 2, Nv >= 2 and a polar rule exact to
+ *    degree Nv + 2 (section "Riemann problem" gives Qp = 3 for the same reason). Qxi <= 1024, Nx >= 1
+ *    (periodic: Nx >= 3), dx > 0, dt > 0.
  */
 #ifndef RLB_H
 #define RLB_H
@@ -60,7 +62,7 @@ enum {
 typedef struct {
   int32_t Qp;       /* radial Gauss-Laguerre order (the paper uses 3) */
   int32_t Qxi;      /* polar Gauss-Legendre order */
-  int32_t Np;       /* radial truncation order of f^eq (the paper uses 2) */
+  int32_t Np;       /* radial truncation order of f^eq (the paper uses 2; at least 2) */
   int32_t Nv;       /* angular truncation order of f^eq (the paper uses 5) */
   int64_t Nx;       /* number of cells */
   double dx;        /* cell width; cell c has its centre at x_left + (c + 1/2) dx */
@@ -125,8 +127,8 @@ int64_t rlb_state_size(rlb_handle h);
 const char *rlb_error_string(rlb_status s);
 
 /*
- * rlb_suggest_dt - time step min(cfl * dx, 1.25 tau): the CFL limit for speeds |xi| <= 1 (section
- *   "Numerical results": "the time step is limited by the CFL condition"; cfl = 0.5 gives the paper's
+ * rlb_suggest_dt - time step min(cfl * dx, 1.25 tau): the CFL bound for particle speeds |xi| <= 1 (the
+ *   paper bounds its step by the CFL condition in section "Numerical results"; cfl = 0.5 gives its
  *   dt = 0.5e-4 at dx = 1e-4) and the SSP-RK3 stability limit of the stiff collision term for |v| <= 0.6.
  *   tau <= 0 or infinite: cfl * dx.
  */

@@ -563,7 +563,7 @@ void free_ctx(rlb_ctx* h) {
 }
 
 rlb_status validate(const rlb_tube* t) {
-  if (t->Qp < 1 || t->Qp > QP_MAX || t->Np < 1 || t->Np >= t->Qp || t->Np > NP_MAX) return RLB_EINVAL;
+  if (t->Qp < 3 || t->Qp > QP_MAX || t->Np < 2 || t->Np >= t->Qp || t->Np > NP_MAX) return RLB_EINVAL;
   if (t->Nv < 2 || t->Nv > NV_MAX || t->Qxi < 1 || t->Qxi > QXI_MAX || 2 * t->Qxi < t->Nv + 3) return RLB_EINVAL;
   if (t->Nx < 1 || t->Nx > (1LL << 30) || (t->bc == RLB_BC_PERIODIC && t->Nx < 3)) return RLB_EINVAL;
   if (t->bc != RLB_BC_OPEN && t->bc != RLB_BC_PERIODIC) return RLB_EINVAL;

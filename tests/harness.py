@@ -1,8 +1,10 @@
 """Glue between the seeded workload specs, the CUDA path (through the C ABI) and the oracle.
 
 Parity rule used by every GPU test: for each row r (one velocity of F, or one field) of one tube,
-    max_x |gpu - oracle| <= rtol * max_x |oracle|,   rtol = 1e-12 (FP64),
-and, for the strictly positive fields (N^0, T^00, T^xx, e, n), also pointwise |gpu - oracle| <= 10 rtol |oracle|.
+    max_x |gpu - oracle| <= rtol * scale_r,   rtol = 1e-12 (FP64),
+with scale_r = max_x |oracle_r| for F and for the positive fields, and the natural magnitude of the
+component for the fields that vanish at rest: max|N^0| for N^x, max|T^00| for T^0x, 1 (the speed of light)
+for v. The positive fields (N^0, T^00, T^xx, e, n) are also checked pointwise: |gpu - oracle| <= 10 rtol |oracle|.
 """
 from __future__ import annotations
 
@@ -80,8 +82,17 @@ def assert_state_parity(gpu: np.ndarray, ref: np.ndarray, rtol: float = RTOL, wh
     return float(e.max())
 
 
+def field_errors(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    own = np.max(np.abs(ref), axis=1)
+    scale = own.copy()
+    scale[1] = max(own[1], own[0])   # N^x against N^0
+    scale[3] = max(own[3], own[2])   # T^0x against T^00
+    scale[6] = max(own[6], 1.0)      # v against c = 1
+    return np.max(np.abs(gpu - ref), axis=1) / np.where(scale > 0, scale, 1.0)
+
+
 def assert_field_parity(gpu: np.ndarray, ref: np.ndarray, rtol: float = RTOL, what: str = "fields"):
-    e = row_errors(gpu, ref)
+    e = field_errors(gpu, ref)
     assert np.all(np.isfinite(gpu)), f"{what}: non-finite values"
     assert e.max() <= rtol, f"{what}: worst field error {e.max():.3e} in field {rb.FIELDS[int(e.argmax())]}"
     for f in POSITIVE_FIELDS:

@@ -64,6 +64,8 @@ def test_invalid_arguments_rejected_before_any_device_call():
     p = one.ctypes.data_as(ctypes.c_void_p)
     bad = [
         rlb.Tube(3, 8, 3, 5, 8, 0.1, 0.01, 1e-3, 0, 0),    # Np >= Qp
+        rlb.Tube(3, 8, 1, 5, 8, 0.1, 0.01, 1e-3, 0, 0),    # Np < 2 cannot recover T^{mu nu}
+        rlb.Tube(2, 8, 1, 5, 8, 0.1, 0.01, 1e-3, 0, 0),    # Qp < 3
         rlb.Tube(3, 3, 2, 5, 8, 0.1, 0.01, 1e-3, 0, 0),    # 2 Qxi < Nv + 3
         rlb.Tube(3, 8, 2, 9, 8, 0.1, 0.01, 1e-3, 0, 0),    # Nv above the supported maximum
         rlb.Tube(5, 8, 2, 5, 8, 0.1, 0.01, 1e-3, 0, 0),    # Qp above the supported maximum
