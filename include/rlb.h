@@ -141,6 +141,40 @@ double rlb_suggest_dt(double dx, double tau, double cfl);
  */
 rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double *pbar, double *wp, double *xi, double *wxi);
 
+/*
+ * rlb_step_static - advance ONE tube by nsteps SSP-RK3 steps without allocating device memory.
+ *   This entry point has no counterpart in the paper; it exists for callers that cannot call cudaMalloc
+ *   (or anything that allocates device memory) at the point where they step: a host application that has
+ *   handed the device memory to its own pool allocator, a plugin whose host forbids device allocation once
+ *   running, or a latency-critical loop where a cudaMalloc, which can synchronise the device, is not
+ *   acceptable. rlb_init allocates the state and scratch buffers of a handle; this call takes the state
+ *   from the caller and keeps its scratch (the two intermediate Runge-Kutta stages, the quadrature tables
+ *   and the tile list) in one file-scope device array of RLB_STATIC_SCRATCH_BYTES bytes that every GPU which
+ *   loads the library holds until the process exits.
+ *   tube:  host pointer to the tube (same rules as rlb_init, bc open or periodic).
+ *   F_in:  device pointer, packed state [Q][Nx] doubles (Q = Qp * Qxi), read only.
+ *   F_out: device pointer, packed state [Q][Nx] doubles, written with the state after nsteps steps; may
+ *          equal F_in (in place). With nsteps = 0 nothing is launched and F_out is left untouched.
+ *   flag:  optional device pointer; a non-physical cell ORs 1 into it (the caller zeroes it). NULL: such
+ *          cells are not reported.
+ *   stream: cudaStream_t to launch on. The call returns once its small host-side tables have been copied
+ *          out (CUDA may first wait for earlier work on that stream, as for any copy from pageable memory);
+ *          the steps themselves run asynchronously.
+ *   Size limit: 2 Q Nx doubles of stage scratch plus the tables (about 8 (Qxi + 16) (NV_MAX + 2) bytes) and
+ *   8 bytes per 63 cells must fit in RLB_STATIC_SCRATCH_BYTES, e.g. Q = 24 up to Nx of about 170000, Q = 600
+ *   up to about 6800; larger tubes return RLB_EINVAL before anything is launched.
+ *   Set-up: the first call on a device (with that device current) looks up the array's device address and
+ *   uploads the series tables that the kernels share with rlb_init; these steps synchronise, so make the first
+ *   call on each device before any stream capture. Later calls only enqueue copies into the array and the
+ *   kernel launches.
+ *   Every call uses the same array and leaves its contents behind: calls that overlap on the GPU (on two
+ *   streams, or from two threads) race on it and must be ordered by the caller.
+ *   Returns RLB_EINVAL for bad arguments or a tube over the limit, RLB_ECUDA if a CUDA call fails.
+ */
+#define RLB_STATIC_SCRATCH_BYTES (64u << 20)
+rlb_status rlb_step_static(const rlb_tube *tube, const double *F_in, double *F_out, int64_t nsteps,
+                           int32_t *flag, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,7 @@ from .binding import (  # noqa: F401
     rlb_set_state,
     rlb_state_size,
     rlb_step,
+    rlb_step_static,
     rlb_suggest_dt,
     rlb_sync,
 )

@@ -91,6 +91,7 @@ def load():
             "rlb_error_string": ([ctypes.c_int], ctypes.c_char_p),
             "rlb_suggest_dt": ([ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_double),
             "rlb_quadrature": ([ip, ip, dp, dp, dp, dp], ctypes.c_int),
+            "rlb_step_static": ([tp, vp, vp, ctypes.c_int64, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -281,3 +282,19 @@ def rlb_quadrature(Qp: int, Qxi: int):
     dp = ctypes.POINTER(ctypes.c_double)
     _check(lib.rlb_quadrature(Qp, Qxi, *[a.ctypes.data_as(dp) for a in out]), "rlb_quadrature")
     return tuple(out)
+
+
+def rlb_step_static(tube: Tube, F_in, F_out, nsteps: int, flag=None, stream=None) -> None:
+    """Allocation-free step of one tube (rlb_step_static): F_in, F_out (may be the same tensor) and the optional
+    int32 flag are CUDA tensors owned by the caller; no device memory is allocated by the library. Meant for
+    callers that cannot allocate device memory while they step (see include/rlb.h)."""
+    n = tube.Qp * tube.Qxi * tube.Nx
+    fp = None
+    if flag is not None:
+        import torch
+
+        if flag.dtype != torch.int32 or not flag.is_cuda:
+            raise ValueError("flag must be an int32 CUDA tensor")
+        fp = ctypes.c_void_p(flag.data_ptr())
+    _check(load().rlb_step_static(ctypes.byref(tube), _dev_ptr(F_in, n), _dev_ptr(F_out, n), int(nsteps), fp,
+                                  _stream(stream)), "rlb_step_static")

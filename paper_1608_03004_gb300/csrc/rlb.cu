@@ -887,3 +887,141 @@ rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double* pbar, double* wp, dou
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------------------------------------------
+// Allocation-free single-tube step (rlb_step_static)
+// --------------------------------------------------------------------------------------------------
+// For callers that cannot allocate device memory when they step. The scratch that rlb_init would allocate
+// (intermediate stages F1 and F2, the tube's tables, its descriptor and tile list, a flag) lives in this
+// file-scope array instead; the existing stage kernel runs on it unchanged.
+namespace {
+
+static __device__ __align__(256) double g_static_scratch[RLB_STATIC_SCRATCH_BYTES / sizeof(double)];
+
+std::mutex g_static_mu;
+double* g_static_addr[64] = {};
+
+// Once per device, with that device current: the device address of the array (in host code the symbol is
+// only a host-side stand-in and must not be passed to a kernel) and the shared series tables.
+rlb_status static_setup(int dev, double** base) {
+  if (dev < 0 || dev >= 64) return RLB_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess || p == nullptr) return e != cudaSuccess ? cuda_status(e) : RLB_ECUDA;
+      g_static_addr[dev] = static_cast<double*>(p);
+    }
+    *base = g_static_addr[dev];
+  }
+  return ensure_series_tables(dev);
+}
+
+size_t align256(size_t bytes) { return (bytes + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, double* F_out, int64_t nsteps,
+                                      int32_t* flag, void* stream) {
+  if (!tube || !F_in || !F_out || nsteps < 0) return RLB_EINVAL;
+  rlb_status st = validate(tube);
+  if (st != RLB_OK) return st;
+  const rlb_tube& t = *tube;
+  const int Q = t.Qp * t.Qxi, Nx = (int)t.Nx;
+  const int ntiles = (Nx + TX - 1) / TX;
+  // layout of the array: descriptor | tiles | flag | tables | F1 | F2, each section 256-byte aligned
+  const size_t off_tiles = align256(sizeof(TubeDev));
+  const size_t off_flag = off_tiles + align256(sizeof(int2) * (size_t)ntiles);
+  const size_t off_tab = off_flag + 256;
+  const size_t off_f1 = off_tab + align256(sizeof(double) * (size_t)tab_size(t.Qxi));
+  const size_t stage_bytes = align256(sizeof(double) * (size_t)Q * (size_t)Nx);
+  const size_t off_f2 = off_f1 + stage_bytes;
+  if (off_f2 + stage_bytes > (size_t)RLB_STATIC_SCRATCH_BYTES) return RLB_EINVAL;
+  if (nsteps == 0) return RLB_OK;
+
+  int dev = 0;
+  RLB_CUDA(cudaGetDevice(&dev));
+  double* base = nullptr;
+  st = static_setup(dev, &base);
+  if (st != RLB_OK) return st;
+  char* b = reinterpret_cast<char*>(base);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // descriptor, tiles and tables on the host, then copied into the array on the caller's stream
+  TubeDev d{};
+  d.Qp = t.Qp;
+  d.Qxi = t.Qxi;
+  d.Np = t.Np;
+  d.Nv = t.Nv;
+  d.bc = t.bc;
+  d.collide = (t.tau > 0.0 && std::isfinite(t.tau)) ? 1 : 0;
+  d.Nx = Nx;
+  d.ld = Nx;  // the caller's packed rows
+  d.off = 0;
+  d.xoff = 0;
+  d.dx = t.dx;
+  d.dt = t.dt;
+  d.inv_tau = d.collide ? 1.0 / t.tau : 0.0;
+  d.x_left = 0.0;
+  d.tab = 0;
+  d.index = 0;
+  std::vector<int2> tiles(ntiles);
+  for (int k = 0; k < ntiles; ++k) tiles[k] = make_int2(0, k * TX);
+  std::vector<double> tab(tab_size(t.Qxi), 0.0), pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
+  if (!rlbq::gauss_laguerre1(t.Qp, pb.data(), wp.data()) || !rlbq::gauss_legendre(t.Qxi, xi.data(), wxi.data()))
+    return RLB_EINVAL;
+  for (int i = 0; i < t.Qp; ++i) {
+    tab[TAB_PBAR + i] = pb[i];
+    tab[TAB_PBAR2 + i] = pb[i] * pb[i];
+    tab[TAB_WP + i] = wp[i];
+    for (int q = 0; q <= t.Np; ++q) {  // K[i][q] = (-1)^q sum_{l=q}^{Np} C(l, q) L^(1)_l(pbar_i)
+      long double acc = 0.0L;
+      for (int l = q; l <= t.Np; ++l) {
+        long double C = 1.0L;
+        for (int u = 1; u <= q; ++u) C = C * (l - q + u) / u;
+        acc += C * rlbq::laguerre1(l, pb[i]);
+      }
+      tab[TAB_K + i * (NP_MAX + 1) + q] = (double)((q % 2) ? -acc : acc);
+    }
+  }
+  for (int j = 0; j < t.Qxi; ++j) {
+    tab[TAB_XI + j] = xi[j];
+    for (int k = 0; k <= NV_MAX; ++k)
+      tab[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
+  }
+  RLB_CUDA(cudaMemcpyAsync(b, &d, sizeof(TubeDev), cudaMemcpyHostToDevice, s));
+  RLB_CUDA(cudaMemcpyAsync(b + off_tiles, tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice, s));
+  RLB_CUDA(cudaMemcpyAsync(b + off_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s));
+  int* dflag = flag ? flag : reinterpret_cast<int*>(b + off_flag);
+  if (!flag) RLB_CUDA(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+  // the copies above come from pageable host memory, so they are consumed before cudaMemcpyAsync returns
+
+  double* F1 = reinterpret_cast<double*>(b + off_f1);
+  double* F2 = reinterpret_cast<double*>(b + off_f2);
+  StageArgs A{};
+  A.tubes = reinterpret_cast<const TubeDev*>(b);
+  A.tiles = reinterpret_cast<const int2*>(b + off_tiles);
+  A.tab = reinterpret_cast<const double*>(b + off_tab);
+  A.flag = dflag;
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const double* Fn = (k == 0) ? F_in : F_out;
+    A.Fn = Fn;
+    A.Fin = Fn;
+    A.Fout = F1;
+    A.a = 0.0;
+    A.b = 1.0;
+    rlb_stage_kernel<<<ntiles, NT, 0, s>>>(A);
+    A.Fin = F1;
+    A.Fout = F2;
+    A.a = 0.75;
+    A.b = 0.25;
+    rlb_stage_kernel<<<ntiles, NT, 0, s>>>(A);
+    A.Fin = F2;
+    A.Fout = F_out;
+    A.a = 1.0 / 3.0;
+    A.b = 2.0 / 3.0;
+    rlb_stage_kernel<<<ntiles, NT, 0, s>>>(A);
+  }
+  return cuda_status(cudaGetLastError());
+}
