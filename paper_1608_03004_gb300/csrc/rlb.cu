@@ -26,9 +26,11 @@
 #include <vector>
 
 #include "../../include/rlb.h"
+#include "rlb_device_math.cuh"
 #include "rlb_internal.h"
 
 using namespace rlb;
+using rlbdev::weno5_corr;
 
 namespace {
 
@@ -39,7 +41,6 @@ constexpr int TX = GW - 1;                 // cells per tile: GW interfaces boun
 constexpr int HALO = 3;                    // WENO5 reaches three cells upwind/downwind
 constexpr int RW = TX + 2 * HALO;          // staged row length
 constexpr int NBC = QP_MAX * (NV_MAX + 1); // per-cell equilibrium coefficients
-constexpr double WENO_EPS = 1e-6;
 
 // Series tables for the Legendre coefficients of (1 - beta xi)^-m (filled once per device):
 //   g_ic[r][k] = (2k+1)/2 * int_{-1}^{1} xi^r P_k(xi) dxi,   g_cb[m][r] = C(m + r - 1, r).
@@ -55,6 +56,7 @@ struct StageArgs {
   const double* tab;
   int* flag;
   double a, b;        // Shu-Osher combination F_out = a F^n + b (F_in + dt L(F_in))
+  int stage;          // 0, 1, 2: selects the b dt xi / dx table
 };
 
 // --------------------------------------------------------------------------------------------------
@@ -81,28 +83,6 @@ __device__ __forceinline__ bool landau(const double mom[5], double& e, double& b
   n = gam * (mom[0] - beta * mom[1]);
   T = e / (3.0 * n);
   return disc >= 0.0 && e > 0.0 && fabs(beta) < 1.0 && n > 0.0 && T > 0.0;
-}
-
-// WENO5 interface value from five samples ordered along the wind (v2 is the upwind cell next to the
-// interface). Same scheme as Jiang & Shu: candidates (2,-7,11)/6, (-1,5,2)/6, (2,5,-1)/6, smoothness
-// indicators with weights 13/12 and 1/4, linear weights (1, 6, 3)/10, alpha_k = d_k/(eps + beta_k)^2.
-// Written on the first differences d_l = v_l - v_{l-1}: 3 beta_k is the quadratic form (4x^2 - 11xy + 10y^2,
-// 4x^2 - 5xy + 4y^2, 10x^2 - 11xy + 4y^2) of adjacent differences, the candidates are
-// v2 + (5 d2 - 2 d1)/6, v2 + (d2 + 2 d3)/6, v2 + (4 d3 - d4)/6, and the common factors of the alphas are
-// cancelled so that only one division remains.
-__device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4) {
-  const double d1 = v1 - v0, d2 = v2 - v1, d3 = v3 - v2, d4 = v4 - v3;
-  const double q1 = d1 * d1, q2 = d2 * d2, q3 = d3 * d3, q4 = d4 * d4;
-  const double p12 = d1 * d2, p23 = d2 * d3, p34 = d3 * d4;
-  const double E = 3.0 * WENO_EPS;
-  const double u0 = fma(4.0, q1, fma(-11.0, p12, fma(10.0, q2, E)));
-  const double u1 = fma(4.0, q2, fma(-5.0, p23, fma(4.0, q3, E)));
-  const double u2 = fma(10.0, q3, fma(-11.0, p34, fma(4.0, q4, E)));
-  const double s0 = u0 * u0, s1 = u1 * u1, s2 = u2 * u2;
-  const double a0 = s1 * s2, a1 = 6.0 * (s0 * s2), a2 = 3.0 * (s0 * s1);
-  const double r0 = fma(5.0, d2, -2.0 * d1), r1 = fma(2.0, d3, d2), r2 = fma(4.0, d3, -d4);
-  const double num = fma(a0, r0, fma(a1, r1, a2 * r2));
-  return v2 + num / (6.0 * (a0 + a1 + a2));
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -213,6 +193,9 @@ __device__ void tile_coeffs(const double* tab, int Qp, CoefSmem& cs, double (*Bs
 // Stage kernel
 // --------------------------------------------------------------------------------------------------
 
+// Barrier of one 64-thread velocity group (named barrier 1 + g; barrier 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(GW) : "memory"); }
+
 struct StageSmem {
   union {
     double red[NG][5][GW];
@@ -278,7 +261,8 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
       sm.u.coef.cell[1][c] = Tt;
       sm.u.coef.cell[2][c] = beta;
       sm.u.coef.ok[c] = ok ? 1 : 0;
-      const double r0 = ok ? T.inv_tau / sqrt(1.0 - beta * beta) : 0.0;
+      // b dt gamma / tau and its beta multiple: the stage's collision rate is r0 - r1 xi_j
+      const double r0 = ok ? (A.b * T.dt) * (T.inv_tau / sqrt(1.0 - beta * beta)) : 0.0;
       sm.rate[0][c] = r0;
       sm.rate[1][c] = r0 * beta;
     }
@@ -287,8 +271,10 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
   }
   __syncthreads();  // sm.src (and, with collisions, the coefficients) are ready
 
-  // C. advection + collision + Runge-Kutta combination, NG velocity rows at a time
-  const double dt = T.dt, inv_dx = 1.0 / T.dx, a = A.a, b = A.b;
+  // C. advection + collision + Runge-Kutta combination, NG velocity rows at a time; each 64-thread group
+  //    works on its own row and synchronises with named barriers only
+  const double a = A.a, b = A.b;
+  const double* cxi_tab = tab + tab_cxi(Qxi) + A.stage * Qxi;
   int buf = 0;
   for (int s0 = 0; s0 < Q; s0 += NG, buf ^= 1) {
     const int s = s0 + g;
@@ -299,31 +285,37 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
       const double* src = Fin + (size_t)s * ld;
       for (int k = c; k < RW; k += GW) row[k] = __ldg(src + sm.src[k]);
     }
-    __syncthreads();
+    group_sync(g);
     const double xi = tab[TAB_XI + j];
-    double phi = 0.0;
+    // interface c lies between cells x0 + c - 1 and x0 + c (row index c + 2 | c + 3); its value is
+    // v2 + G with v2 the upwind cell; the flux difference of cell x0 + c is D + G_{c+1} - G_c with D the
+    // difference of the two upwind cells
+    double G = 0.0, D = 0.0;
     if (rv) {
-      // interface c lies between cells x0 + c - 1 and x0 + c (row index c + 2 | c + 3)
-      if (xi > 0.0)
-        phi = weno5(row[c], row[c + 1], row[c + 2], row[c + 3], row[c + 4]);
-      else
-        phi = weno5(row[c + 5], row[c + 4], row[c + 3], row[c + 2], row[c + 1]);
+      if (xi > 0.0) {
+        G = weno5_corr(row[c], row[c + 1], row[c + 2], row[c + 3], row[c + 4]);
+        D = row[c + 3] - row[c + 2];
+      } else {
+        G = weno5_corr(row[c + 5], row[c + 4], row[c + 3], row[c + 2], row[c + 1]);
+        D = row[c + 4] - row[c + 3];
+      }
     }
-    sm.phi[buf][g][c] = phi;
-    __syncthreads();
+    sm.phi[buf][g][c] = G;
+    group_sync(g);
     if (rv && cell) {
       const double F = row[c + 3];
-      double L = -(xi * inv_dx) * (sm.phi[buf][g][c + 1] - phi);
+      const double dphi = D + (sm.phi[buf][g][c + 1] - G);
+      double out = F;
+      if (a != 0.0) out = fma(a, Fn[(size_t)s * ld + x], b * F);
+      out = fma(-cxi_tab[j], dphi, out);  // - b dt xi/dx (Phi_{x+1/2} - Phi_{x-1/2})
       if (T.collide) {
         const double* pw = tab + TAB_XI + Qxi + j * (NV_MAX + 1);
         double feq = 0.0;
 #pragma unroll
         for (int k = 0; k <= NVc; ++k) feq = fma(sm.B[i * (NV_MAX + 1) + k][c], pw[k], feq);
         const double rate = fma(-sm.rate[1][c], xi, sm.rate[0][c]);
-        L = fma(-rate, F - feq, L);
+        out = fma(rate, feq - F, out);  // + b dt gamma (1 - beta xi)/tau (F^eq - F)
       }
-      double out = b * fma(dt, L, F);
-      if (a != 0.0) out = fma(a, Fn[(size_t)s * ld + x], out);
       Fout[(size_t)s * ld + x] = out;
     }
   }
@@ -588,7 +580,6 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   h->tubes.assign(tubes, tubes + ntubes);
   // quadrature tables, one block per tube
   std::vector<double> tab;
-  std::map<std::pair<int, int>, int> seen;  // one table block per (Qp, Np, Nv, Qxi)
   h->td.resize(ntubes);
   long long off = 0, xoff = 0;
   for (int b = 0; b < ntubes; ++b) {
@@ -612,14 +603,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     off += (long long)t.Qp * t.Qxi * d.ld;
     xoff += t.Nx;
     h->packed += (long long)t.Qp * t.Qxi * t.Nx;
-    auto key = std::make_pair(t.Qp * 1000 + t.Np * 100 + t.Nv, t.Qxi);
-    auto it = seen.find(key);
-    if (it != seen.end()) {
-      d.tab = it->second;
-      continue;
-    }
     d.tab = (int)tab.size();
-    seen[key] = d.tab;
     tab.resize(tab.size() + tab_size(t.Qxi), 0.0);
     double* T = tab.data() + d.tab;
     std::vector<double> pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
@@ -644,6 +628,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
       T[TAB_XI + j] = xi[j];
       for (int k = 0; k <= NV_MAX; ++k)
         T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
+      for (int st = 0; st < 3; ++st) T[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
     }
   }
   h->state_elems = off;
@@ -775,23 +760,17 @@ rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
   A.tab = h->d_tab;
   A.flag = h->d_flag;
   A.Fn = h->F;
-  for (int64_t t = 0; t < nsteps; ++t) {
-    A.Fin = h->F;
-    A.Fout = h->F1;
-    A.a = 0.0;
-    A.b = 1.0;
-    rlb_stage_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
-    A.Fin = h->F1;
-    A.Fout = h->F2;
-    A.a = 0.75;
-    A.b = 0.25;
-    rlb_stage_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
-    A.Fin = h->F2;
-    A.Fout = h->F;
-    A.a = 1.0 / 3.0;
-    A.b = 2.0 / 3.0;
-    rlb_stage_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
-  }
+  const double* in[3] = {h->F, h->F1, h->F2};
+  double* out[3] = {h->F1, h->F2, h->F};
+  for (int64_t t = 0; t < nsteps; ++t)
+    for (int st = 0; st < 3; ++st) {
+      A.Fin = in[st];
+      A.Fout = out[st];
+      A.a = RK_A[st];
+      A.b = RK_B[st];
+      A.stage = st;
+      rlb_stage_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
+    }
   return cuda_status(cudaGetLastError());
 }
 
@@ -989,6 +968,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
     tab[TAB_XI + j] = xi[j];
     for (int k = 0; k <= NV_MAX; ++k)
       tab[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
+    for (int st = 0; st < 3; ++st) tab[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
   }
   RLB_CUDA(cudaMemcpyAsync(b, &d, sizeof(TubeDev), cudaMemcpyHostToDevice, s));
   RLB_CUDA(cudaMemcpyAsync(b + off_tiles, tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice, s));
@@ -1006,22 +986,17 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
   A.flag = dflag;
   for (int64_t k = 0; k < nsteps; ++k) {
     const double* Fn = (k == 0) ? F_in : F_out;
+    const double* in[3] = {Fn, F1, F2};
+    double* out[3] = {F1, F2, F_out};
     A.Fn = Fn;
-    A.Fin = Fn;
-    A.Fout = F1;
-    A.a = 0.0;
-    A.b = 1.0;
-    rlb_stage_kernel<<<ntiles, NT, 0, s>>>(A);
-    A.Fin = F1;
-    A.Fout = F2;
-    A.a = 0.75;
-    A.b = 0.25;
-    rlb_stage_kernel<<<ntiles, NT, 0, s>>>(A);
-    A.Fin = F2;
-    A.Fout = F_out;
-    A.a = 1.0 / 3.0;
-    A.b = 2.0 / 3.0;
-    rlb_stage_kernel<<<ntiles, NT, 0, s>>>(A);
+    for (int st = 0; st < 3; ++st) {
+      A.Fin = in[st];
+      A.Fout = out[st];
+      A.a = RK_A[st];
+      A.b = RK_B[st];
+      A.stage = st;
+      rlb_stage_kernel<<<ntiles, NT, 0, s>>>(A);
+    }
   }
   return cuda_status(cudaGetLastError());
 }

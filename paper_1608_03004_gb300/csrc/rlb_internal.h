@@ -3,6 +3,11 @@
 
 #include <cstdint>
 
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
 namespace rlbq {
 bool gauss_legendre(int n, double* x, double* w);
 bool gauss_laguerre1(int n, double* x, double* w);
@@ -42,13 +47,17 @@ struct TubeDev {
 //   [3 QP_MAX, 3 QP_MAX + QP_MAX (NP_MAX+1))   K[i][q] = (-1)^q sum_{l=q}^{Np} C(l,q) L^(1)_l(pbar_i)
 //                                               at [i (NP_MAX+1) + q]: the radial factor multiplying
 //                                               s^(q+2) hhat_{q+2,k} in the truncated equilibrium
-//   then xi_j (Qxi), then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k] (Qxi (NV_MAX+1)), zero for k > Nv
+//   then xi_j (Qxi), then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k] (Qxi (NV_MAX+1)), zero for k > Nv,
+//   then b_st dt xi_j / dx at [st Qxi + j] for the three Runge-Kutta stages, b = (1, 1/4, 2/3)
 constexpr int TAB_PBAR = 0;
 constexpr int TAB_PBAR2 = QP_MAX;
 constexpr int TAB_WP = 2 * QP_MAX;
 constexpr int TAB_K = 3 * QP_MAX;
 constexpr int TAB_XI = TAB_K + QP_MAX * (NP_MAX + 1);
-inline int tab_pw(int Qxi) { return TAB_XI + Qxi; }
-inline int tab_size(int Qxi) { return TAB_XI + Qxi + Qxi * (NV_MAX + 1); }
+__host__ __device__ inline int tab_pw(int Qxi) { return TAB_XI + Qxi; }
+__host__ __device__ inline int tab_cxi(int Qxi) { return TAB_XI + Qxi + Qxi * (NV_MAX + 1); }
+inline int tab_size(int Qxi) { return tab_cxi(Qxi) + 3 * Qxi; }
+constexpr double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};  // Shu-Osher SSP-RK3: F_out = a F^n + b (F_in + dt L(F_in))
+constexpr double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
 
 }  // namespace rlb

@@ -1,0 +1,35 @@
+// Test-only shim: evaluates the library's device reciprocal and WENO5 correction on host-provided inputs.
+// Built by tests/test_device_math_gpu.py with nvcc; not part of the library.
+#include <cuda_runtime.h>
+
+#include "../../paper_1608_03004_gb300/csrc/rlb_device_math.cuh"
+
+__global__ void rcp_kernel(const double* d, double* out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = rlbdev::rcp_nr(d[i]);
+}
+
+__global__ void weno_kernel(const double* v, double* out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double* w = v + 5 * i;
+    out[i] = w[2] + rlbdev::weno5_corr(w[0], w[1], w[2], w[3], w[4]);
+  }
+}
+
+extern "C" int dm_eval(int which, const double* in, double* out, int n) {
+  double *din = nullptr, *dout = nullptr;
+  const size_t nin = (size_t)n * (which == 0 ? 1 : 5);
+  if (cudaMalloc(&din, nin * sizeof(double)) != cudaSuccess) return 1;
+  if (cudaMalloc(&dout, (size_t)n * sizeof(double)) != cudaSuccess) return 2;
+  cudaMemcpy(din, in, nin * sizeof(double), cudaMemcpyHostToDevice);
+  const int nb = (n + 255) / 256;
+  if (which == 0)
+    rcp_kernel<<<nb, 256>>>(din, dout, n);
+  else
+    weno_kernel<<<nb, 256>>>(din, dout, n);
+  cudaError_t e = cudaMemcpy(out, dout, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(din);
+  cudaFree(dout);
+  return e == cudaSuccess ? 0 : 3;
+}

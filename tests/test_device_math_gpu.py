@@ -1,0 +1,60 @@
+"""GPU unit tests of the stage kernel's device arithmetic (csrc/rlb_device_math.cuh):
+* rcp_nr: hardware reciprocal approximation + one cubic Newton-Raphson step, against IEEE division (numpy);
+* weno5_corr: the first-difference form of WENO5 with cancelled common factors, against the oracle's
+  textbook Jiang-Shu formula on random, smooth, stepped and tiny data."""
+import ctypes
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_03004_gb300 import build as B
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def shim():
+    out = os.path.join(tempfile.mkdtemp(prefix="rlb_dm_"), "libdm.so")
+    subprocess.run([B.nvcc(), B.ARCH, "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", out,
+                    os.path.join(HERE, "gpu_src", "device_math_check.cu")], check=True)
+    lib = ctypes.CDLL(out)
+    lib.dm_eval.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    yield lib
+    shutil.rmtree(os.path.dirname(out), ignore_errors=True)
+
+
+def run(lib, which, x, n):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(n)
+    assert lib.dm_eval(which, x.ctypes.data, y.ctypes.data, n) == 0
+    return y
+
+
+def test_reciprocal_within_two_ulp(shim):
+    rng = np.random.default_rng(1)
+    d = np.exp(rng.uniform(-60, 60, 1 << 20))
+    r = run(shim, 0, d, d.size)
+    rel = np.abs(r * d - 1.0)
+    assert rel.max() <= 2.5 * 2.0**-53 * 2, rel.max()
+
+
+def test_weno5_matches_oracle(shim):
+    rng = np.random.default_rng(2)
+    cases = []
+    for scale in (1e-8, 1e-3, 1.0, 10.0):
+        cases.append(scale * rng.normal(size=(4000, 5)))                      # rough data
+        base = rng.uniform(0.1, 1.0, size=(4000, 1)) * scale
+        cases.append(base + 1e-3 * scale * np.cumsum(rng.normal(size=(4000, 5)), axis=1))  # smooth
+        step = np.where(np.arange(5) >= rng.integers(1, 5, size=(4000, 1)), 1.0, 0.1) * scale
+        cases.append(step)                                                    # jumps
+    v = np.concatenate(cases)
+    got = run(shim, 1, v, v.shape[0])
+    ref = np.array([oracle.weno5(*row) for row in v])
+    err = np.abs(got - ref) / np.max(np.abs(v), axis=1)
+    assert err.max() < 1e-14, err.max()
