@@ -161,7 +161,7 @@ rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double *pbar, double *wp, dou
  *          out (CUDA may first wait for earlier work on that stream, as for any copy from pageable memory);
  *          the steps themselves run asynchronously.
  *   Size limit: 2 Q Nx doubles of stage scratch plus the tables (about 8 (Qxi + 16) (NV_MAX + 2) bytes) and
- *   8 bytes per 63 cells must fit in RLB_STATIC_SCRATCH_BYTES, e.g. Q = 24 up to Nx of about 170000, Q = 600
+ *   8 bytes per 61 cells must fit in RLB_STATIC_SCRATCH_BYTES, e.g. Q = 24 up to Nx of about 170000, Q = 600
  *   up to about 6800; larger tubes return RLB_EINVAL before anything is launched.
  *   Set-up: the first call on a device (with that device current) looks up the array's device address and
  *   uploads the series tables that the kernels share with rlb_init; these steps synchronise, so make the first

@@ -3,13 +3,14 @@
 // its C ABI (include/rlb.h).
 //
 // One SSP-RK3 stage is one launch of rlb_stage_kernel over every tile of every tube. A CTA owns a tile of
-// TX = 63 cells of one tube and, for those cells:
+// TX = 61 cells of one tube and, for those cells:
 //   A. reduces F over all Q velocities to N^0, N^x, T^00, T^0x, T^xx (section "Relativistic lattice
 //      Boltzmann equation");
 //   B. solves the Landau-frame eigenproblem T^mu_nu u^nu = -e u^mu for e, v, n and builds the per-cell
 //      coefficients of the truncated equilibrium of Eq. (feqtrunc);
 //   C. walks the velocity rows four at a time: stages the row (tile + 3-cell halo, boundary condition
-//      folded into the load) in shared memory, reconstructs the 64 interface values with WENO5 and writes
+//      folded into the load) in shared memory, evaluates the WENO5 smoothness indicators once per pair of
+//      adjacent first differences, combines three pairs into each of the 62 interface values and writes
 //      F_out = a F^n + b (F_in + dt L(F_in)), L = advection + Anderson-Witting collision (Eq. (Boltz)).
 // The step is FP64 throughout; on GB300 the FP64 pipe (about 2 DFMA per SM per clock) bounds it, so the
 // arithmetic is arranged to spend as few FP64 instructions per velocity-node update as possible.
@@ -30,14 +31,15 @@
 #include "rlb_internal.h"
 
 using namespace rlb;
-using rlbdev::weno5_corr;
+using rlbdev::weno5_combine;
+using rlbdev::weno5_pair;
 
 namespace {
 
 constexpr int NT = 256;                    // threads per CTA
 constexpr int GW = 64;                     // threads per velocity group (one row at a time)
 constexpr int NG = NT / GW;                // velocity rows processed together
-constexpr int TX = GW - 1;                 // cells per tile: GW interfaces bound TX cells
+constexpr int TX = GW - 3;                 // cells per tile: their TX + 1 interfaces need GW indicator pairs
 constexpr int HALO = 3;                    // WENO5 reaches three cells upwind/downwind
 constexpr int RW = TX + 2 * HALO;          // staged row length
 constexpr int NBC = QP_MAX * (NV_MAX + 1); // per-cell equilibrium coefficients
@@ -203,9 +205,11 @@ struct StageSmem {
   } u;
   double B[NBC][GW];
   double rate[2][GW];
-  double row[2][NG][RW + 3];
-  double phi[2][NG][GW];
-  int src[RW + 3];  // source cell of each staged position (boundary condition applied)
+  double row[2][NG][RW + 1];  // staged velocity rows (double-buffered: written before the first barrier)
+  double d1[NG][RW + 1];      // first differences by position, d1[k] = row[k] - row[k-1]
+  double sp[NG][3][GW];       // scaled indicator squares, one triple per pair of adjacent differences
+  double phi[NG][GW];         // WENO correction G of each interface
+  int src[RW + 1];            // source cell of each staged position (boundary condition applied)
 };
 
 template <int NPc, int NVc>
@@ -275,6 +279,11 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
   //    works on its own row and synchronises with named barriers only
   const double a = A.a, b = A.b;
   const double* cxi_tab = tab + tab_cxi(Qxi) + A.stage * Qxi;
+  double* d1 = sm.d1[g];
+  double* sp0 = sm.sp[g][0];
+  double* sp1 = sm.sp[g][1];
+  double* sp2 = sm.sp[g][2];
+  double* phi = sm.phi[g];
   int buf = 0;
   for (int s0 = 0; s0 < Q; s0 += NG, buf ^= 1) {
     const int s = s0 + g;
@@ -287,24 +296,40 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
     }
     group_sync(g);
     const double xi = tab[TAB_XI + j];
-    // interface c lies between cells x0 + c - 1 and x0 + c (row index c + 2 | c + 3); its value is
-    // v2 + G with v2 the upwind cell; the flux difference of cell x0 + c is D + G_{c+1} - G_c with D the
-    // difference of the two upwind cells
-    double G = 0.0, D = 0.0;
+    const bool fwd = xi > 0.0;
+    // pairs: thread c owns the pair of differences at positions (p, p + 1), p = c + 1 (wind toward +x) or
+    // c + 2 (toward -x); these are the pairs the TX + 1 interfaces of the tile use
     if (rv) {
-      if (xi > 0.0) {
-        G = weno5_corr(row[c], row[c + 1], row[c + 2], row[c + 3], row[c + 4]);
-        D = row[c + 3] - row[c + 2];
-      } else {
-        G = weno5_corr(row[c + 5], row[c + 4], row[c + 3], row[c + 2], row[c + 1]);
-        D = row[c + 4] - row[c + 3];
-      }
+      const int p = c + (fwd ? 1 : 2);
+      const double x = row[p] - row[p - 1], y = row[p + 1] - row[p];
+      double sa, sb, sc;
+      weno5_pair(x, y, fwd, sa, sb, sc);
+      sp0[c] = sa;
+      sp1[c] = sb;
+      sp2[c] = sc;
+      d1[p] = x;
+      if (c == GW - 1) d1[p + 1] = y;
     }
-    sm.phi[buf][g][c] = G;
+    group_sync(g);
+    // interfaces: interface c lies between cells x0 + c - 1 and x0 + c (row index c + 2 | c + 3); its value
+    // is v2 + G with v2 the upwind cell; D = v2(c + 1) - v2(c) is the memory-order difference d1[c + 3]
+    // (wind toward +x) or d1[c + 4] (toward -x)
+    double D = 0.0;
+    if (rv && c <= TX) {
+      double G;
+      if (fwd) {
+        D = d1[c + 3];
+        G = weno5_combine(sp0[c], sp1[c + 1], sp2[c + 2], d1[c + 1], d1[c + 2], D, d1[c + 4]);
+      } else {
+        D = d1[c + 4];
+        G = weno5_combine(sp0[c + 2], sp1[c + 1], sp2[c], -d1[c + 5], -D, -d1[c + 3], -d1[c + 2]);
+      }
+      phi[c] = G;
+    }
     group_sync(g);
     if (rv && cell) {
       const double F = row[c + 3];
-      const double dphi = D + (sm.phi[buf][g][c + 1] - G);
+      const double dphi = D + (phi[c + 1] - phi[c]);
       double out = F;
       if (a != 0.0) out = fma(a, Fn[(size_t)s * ld + x], b * F);
       out = fma(-cxi_tab[j], dphi, out);  // - b dt xi/dx (Phi_{x+1/2} - Phi_{x-1/2})
@@ -321,8 +346,9 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
   }
 }
 
-__global__ void __launch_bounds__(NT) rlb_stage_kernel(StageArgs A) {
-  __shared__ StageSmem sm;
+__global__ void __launch_bounds__(NT, 4) rlb_stage_kernel(StageArgs A) {
+  extern __shared__ __align__(16) unsigned char stage_smem_raw[];
+  StageSmem& sm = *reinterpret_cast<StageSmem*>(stage_smem_raw);
   const int2 tl = A.tiles[blockIdx.x];
   const TubeDev T = A.tubes[tl.x];
   if (T.Np == 2 && T.Nv == 5)
@@ -488,7 +514,8 @@ rlb_status cuda_status(cudaError_t e) {
 std::mutex g_tables_mu;
 bool g_tables_ready[64] = {};
 
-// Fill the series tables of this device once (long double on the host).
+// Once per device: fill the series tables (long double on the host) and let the stage kernel use more than
+// 48 KB of dynamic shared memory.
 rlb_status ensure_series_tables(int dev) {
   std::lock_guard<std::mutex> lk(g_tables_mu);
   if (dev < 0 || dev >= 64) return RLB_EINVAL;
@@ -513,6 +540,8 @@ rlb_status ensure_series_tables(int dev) {
   }
   RLB_CUDA(cudaMemcpyToSymbol(g_ic, ic.data(), ic.size() * sizeof(double)));
   RLB_CUDA(cudaMemcpyToSymbol(g_cb, cb.data(), cb.size() * sizeof(double)));
+  RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(StageSmem)));
   g_tables_ready[dev] = true;
   return RLB_OK;
 }
@@ -769,7 +798,7 @@ rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
       A.a = RK_A[st];
       A.b = RK_B[st];
       A.stage = st;
-      rlb_stage_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
+      rlb_stage_kernel<<<h->ntiles, NT, sizeof(StageSmem), h->stream>>>(A);
     }
   return cuda_status(cudaGetLastError());
 }
@@ -995,7 +1024,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
       A.a = RK_A[st];
       A.b = RK_B[st];
       A.stage = st;
-      rlb_stage_kernel<<<ntiles, NT, 0, s>>>(A);
+      rlb_stage_kernel<<<ntiles, NT, sizeof(StageSmem), s>>>(A);
     }
   }
   return cuda_status(cudaGetLastError());

@@ -1,5 +1,5 @@
-// Device arithmetic of the stage kernel that is worth testing on its own: the reciprocal and the WENO5
-// interface correction. Included by rlb.cu and by the GPU unit test of these two functions.
+// Device arithmetic of the stage kernel that is worth testing on its own: the reciprocal and the two halves
+// of the WENO5 interface value. Included by rlb.cu and by the GPU unit test of these functions.
 #pragma once
 
 namespace rlbdev {
@@ -17,32 +17,60 @@ __device__ __forceinline__ double rcp_nr(double d) {
 
 constexpr double WENO_EPS = 1e-6;
 
-// Fifth-order WENO (Jiang & Shu) interface value from five samples ordered along the wind, v2 being the
-// upwind cell next to the interface; returns G with interface value v2 + G.
-//   Candidates (2,-7,11)/6, (-1,5,2)/6, (2,5,-1)/6 = v2 + r_k/6 with r0 = 5 d2 - 2 d1, r1 = d2 + 2 d3,
-//   r2 = 4 d3 - d4 on the first differences d_l = v_l - v_{l-1}.
-//   Smoothness indicators (weights 13/12 and 1/4): 3 beta_k are the quadratic forms 4x^2 - 11xy + 10y^2,
-//   4x^2 - 5xy + 4y^2, 10x^2 - 11xy + 4y^2 of adjacent differences.
-//   alpha_k = d_k / (eps + beta_k)^2 with d = (1, 6, 3)/10 equals 9 / u_k^2 for
-//   u_k = (3 eps + 3 beta_k) / sqrt(d_k), so the normalised weights are w_k = prod_{l!=k} s_l / sum_m
-//   prod_{l!=m} s_l with s_k = u_k^2 (the sqrt(1/d_k) factors are folded into the coefficients).
-__device__ __forceinline__ double weno5_corr(double v0, double v1, double v2, double v3, double v4) {
-  constexpr double c0 = 3.1622776601683795;  // sqrt(10)
-  constexpr double c1 = 1.2909944487358056;  // sqrt(10/6)
-  constexpr double c2 = 1.8257418583505538;  // sqrt(10/3)
-  constexpr double E = 3.0 * WENO_EPS;
-  const double d1 = v1 - v0, d2 = v2 - v1, d3 = v3 - v2, d4 = v4 - v3;
-  const double q1 = d1 * d1, q2 = d2 * d2, q3 = d3 * d3, q4 = d4 * d4;
-  const double p12 = d1 * d2, p23 = d2 * d3, p34 = d3 * d4;
-  const double u0 = fma(4.0 * c0, q1, fma(-11.0 * c0, p12, fma(10.0 * c0, q2, E * c0)));
-  const double u1 = fma(4.0 * c1, q2, fma(-5.0 * c1, p23, fma(4.0 * c1, q3, E * c1)));
-  const double u2 = fma(10.0 * c2, q3, fma(-11.0 * c2, p34, fma(4.0 * c2, q4, E * c2)));
-  const double s0 = u0 * u0, s1 = u1 * u1, s2 = u2 * u2;
+// Fifth-order WENO (Jiang & Shu) written on first differences d_l = v_l - v_{l-1} of five samples
+// v0..v4 ordered along the wind (v2 is the upwind cell next to the interface, whose value is v2 + G):
+//   candidates (2,-7,11)/6, (-1,5,2)/6, (2,5,-1)/6  =  v2 + r_k/6,  r0 = 5 d2 - 2 d1, r1 = d2 + 2 d3,
+//   r2 = 4 d3 - d4;
+//   smoothness indicators (weights 13/12 and 1/4): 3 beta_k = SL(d1,d2), SC(d2,d3), SR(d3,d4) with
+//   SL(x,y) = 4x^2 - 11xy + 10y^2, SC = 4x^2 - 5xy + 4y^2, SR = 10x^2 - 11xy + 4y^2;
+//   alpha_k = d_k / (eps + beta_k)^2 with d = (1, 6, 3)/10 equals 9 / s_k, s_k = u_k^2,
+//   u_k = (3 eps + 3 beta_k) / sqrt(d_k); the normalised weights are w_k = prod_{l!=k} s_l / sum_m prod_{l!=m} s_l.
+// Each indicator depends on one pair of adjacent differences, and each pair serves three interfaces, so
+// the kernel evaluates the three scaled squares once per pair (weno5_pair) and combines three pairs per
+// interface (weno5_combine). For a wind toward decreasing index the stencil is mirrored: the differences
+// change sign and order, which swaps the roles of SL and SR.
+constexpr double C0 = 3.1622776601683795;  // sqrt(10)
+constexpr double C1 = 1.2909944487358056;  // sqrt(10/6)
+constexpr double C2 = 1.8257418583505538;  // sqrt(10/3)
+constexpr double E3 = 3.0 * WENO_EPS;
+
+// Scaled indicator squares of the pair (x, y) = (d_j, d_{j+1}) in memory order. fwd: wind toward increasing
+// index; then sA = (C0 (SL + 3eps))^2, sB = (C1 (SC + 3eps))^2, sC = (C2 (SR + 3eps))^2; otherwise SL and SR
+// trade places.
+__device__ __forceinline__ void weno5_pair(double x, double y, bool fwd, double& sA, double& sB, double& sC) {
+  const double qx = x * x, pxy = x * y, qy = y * y;
+  const double ax = fwd ? 4.0 * C0 : 10.0 * C0, ay = fwd ? 10.0 * C0 : 4.0 * C0;
+  const double cx = fwd ? 10.0 * C2 : 4.0 * C2, cy = fwd ? 4.0 * C2 : 10.0 * C2;
+  const double uA = fma(ax, qx, fma(-11.0 * C0, pxy, fma(ay, qy, E3 * C0)));
+  const double uB = fma(4.0 * C1, qx, fma(-5.0 * C1, pxy, fma(4.0 * C1, qy, E3 * C1)));
+  const double uC = fma(cx, qx, fma(-11.0 * C2, pxy, fma(cy, qy, E3 * C2)));
+  sA = uA * uA;
+  sB = uB * uB;
+  sC = uC * uC;
+}
+
+// G of the interface from the three scaled squares (s0, s1, s2) of its stencils and the differences
+// d1..d4 in wind order.
+__device__ __forceinline__ double weno5_combine(double s0, double s1, double s2, double d1, double d2, double d3,
+                                                double d4) {
   const double r0 = fma(5.0, d2, -2.0 * d1), r1 = fma(2.0, d3, d2), r2 = fma(4.0, d3, -d4);
   const double a0 = s1 * s2;
   const double num = fma(s0, fma(s2, r1, s1 * r2), a0 * r0);
   const double den = fma(s0, s1 + s2, a0);
   return num * rcp_nr(6.0 * den);
+}
+
+// Interface value v2 + G of five samples in memory order m0..m4 around the interface between m2 and m3
+// (wind toward increasing index, fwd) or between m1 and m2 (wind toward decreasing index), computed
+// exactly as the stage kernel does: pairs first, then the combination.
+__device__ __forceinline__ double weno5_interface(double m0, double m1, double m2, double m3, double m4, bool fwd) {
+  const double D1 = m1 - m0, D2 = m2 - m1, D3 = m3 - m2, D4 = m4 - m3;
+  double a[3], b[3], c[3];
+  weno5_pair(D1, D2, fwd, a[0], b[0], c[0]);
+  weno5_pair(D2, D3, fwd, a[1], b[1], c[1]);
+  weno5_pair(D3, D4, fwd, a[2], b[2], c[2]);
+  if (fwd) return m2 + weno5_combine(a[0], b[1], c[2], D1, D2, D3, D4);
+  return m2 + weno5_combine(a[2], b[1], c[0], -D4, -D3, -D2, -D1);
 }
 
 }  // namespace rlbdev

@@ -9,11 +9,13 @@ __global__ void rcp_kernel(const double* d, double* out, int n) {
   if (i < n) out[i] = rlbdev::rcp_nr(d[i]);
 }
 
-__global__ void weno_kernel(const double* v, double* out, int n) {
+// which = 1: wind toward increasing index, samples in memory order = wind order;
+// which = 2: wind toward decreasing index, samples in memory order (interface between m1 and m2).
+__global__ void weno_kernel(const double* v, double* out, int n, bool fwd) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     const double* w = v + 5 * i;
-    out[i] = w[2] + rlbdev::weno5_corr(w[0], w[1], w[2], w[3], w[4]);
+    out[i] = rlbdev::weno5_interface(w[0], w[1], w[2], w[3], w[4], fwd);
   }
 }
 
@@ -27,7 +29,7 @@ extern "C" int dm_eval(int which, const double* in, double* out, int n) {
   if (which == 0)
     rcp_kernel<<<nb, 256>>>(din, dout, n);
   else
-    weno_kernel<<<nb, 256>>>(din, dout, n);
+    weno_kernel<<<nb, 256>>>(din, dout, n, which == 1);
   cudaError_t e = cudaMemcpy(out, dout, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(din);
   cudaFree(dout);

@@ -1,7 +1,8 @@
 """GPU unit tests of the stage kernel's device arithmetic (csrc/rlb_device_math.cuh):
 * rcp_nr: hardware reciprocal approximation + one cubic Newton-Raphson step, against IEEE division (numpy);
-* weno5_corr: the first-difference form of WENO5 with cancelled common factors, against the oracle's
-  textbook Jiang-Shu formula on random, smooth, stepped and tiny data."""
+* weno5_pair + weno5_combine (the kernel's WENO5: indicators per pair of differences, then three pairs per
+  interface) for both wind directions, against the oracle's textbook Jiang-Shu formula on random, smooth,
+  stepped and tiny data."""
 import ctypes
 import os
 import shutil
@@ -54,7 +55,12 @@ def test_weno5_matches_oracle(shim):
         step = np.where(np.arange(5) >= rng.integers(1, 5, size=(4000, 1)), 1.0, 0.1) * scale
         cases.append(step)                                                    # jumps
     v = np.concatenate(cases)
+    scale = np.max(np.abs(v), axis=1)
+    # wind toward +x: memory order is wind order
     got = run(shim, 1, v, v.shape[0])
     ref = np.array([oracle.weno5(*row) for row in v])
-    err = np.abs(got - ref) / np.max(np.abs(v), axis=1)
-    assert err.max() < 1e-14, err.max()
+    assert (np.abs(got - ref) / scale).max() < 1e-14
+    # wind toward -x: the oracle sees the samples in reverse (wind) order
+    got = run(shim, 2, v, v.shape[0])
+    ref = np.array([oracle.weno5(*row[::-1]) for row in v])
+    assert (np.abs(got - ref) / scale).max() < 1e-14
