@@ -6,7 +6,11 @@ Nx = 4096, Qp = 3, tau in {1e-4, 1e-3, 1e-2, 1e-1, 1, 10, inf} x Qxi in {8, 32, 
 velocity nodes, all advanced together, one handle, FP64. A step is one SSP-RK3 time step of every tube
 (three launches of the stage kernel). One velocity-node update = one velocity at one cell over one step.
 
-    python bench.py [--steps K] [--warmup W] [--workload sweep|small|stress] [--impl ours|reference]
+    python bench.py [--steps K] [--warmup W] [--workload sweep|small|stress] [--precision f64|f32|bf16]
+                    [--impl ours|reference]
+
+--precision f32/bf16 stores F in that type (FP32 arithmetic, compensated moments reduced in FP64, FP64 Landau
+solve); its roofline is HBM (algorithmic 8 x element size bytes per velocity node per step).
 
 Prints one JSON line. Under torchrun every rank advances its own copy of the workload (weak scaling, no
 collective on the data path); the time is the max over ranks.
@@ -43,8 +47,14 @@ FLOPS_PER_NODE_STAGE = 84
 # Algorithmic HBM bytes per velocity node per step with one launch per stage: stage inputs read once
 # (1 + 2 + 2 doubles), outputs written once (3 doubles).
 BYTES_PER_NODE_STEP = 64
-PROFILE = os.path.join(ROOT, "profiles", "rlb_stage_kernel_sod_sweep.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1608_03004_gb300", "csrc", "rlb.cu")
+PROFILES = {"f64": os.path.join(ROOT, "profiles", "rlb_stage_kernel_sod_sweep.md"),
+            "f32": os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_f32_stress.md"),
+            "bf16": os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_bf16_stress.md")}
+KERNEL_SRCS = {"f64": [os.path.join(ROOT, "paper_1608_03004_gb300", "csrc", "rlb.cu")],
+               "f32": [os.path.join(ROOT, "paper_1608_03004_gb300", "csrc", "rlb_stage_rp.cuh")],
+               "bf16": [os.path.join(ROOT, "paper_1608_03004_gb300", "csrc", "rlb_stage_rp.cuh")]}
+ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
+CPU_SAMPLE_NODES = 24_000_000  # bound on the velocity nodes the oracle advances per CPU sample step
 
 
 def workload(name: str):
@@ -188,16 +198,36 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def cpu_sample(specs):
+    """The workload itself if small enough, else windows of at most 4096 cells cut from its tubes (each window
+    an independent tube with the same orders, grid spacing, time step and relaxation time) up to about
+    CPU_SAMPLE_NODES velocity nodes. Returns (specs, description)."""
+    if W.total_nodes(specs) <= CPU_SAMPLE_NODES:
+        return specs, f"every tube of the workload ({W.total_nodes(specs)} velocity nodes)"
+    out, nodes, k = [], 0, 0
+    while nodes < CPU_SAMPLE_NODES and k < 10000:
+        base = specs[k % len(specs)]
+        nx = min(base.Nx, 4096)
+        win = W.TubeSpec(Nx=nx, Qxi=base.Qxi, tau=base.tau, dt=base.dt, dx=base.dx, Qp=base.Qp, Np=base.Np,
+                         Nv=base.Nv, bc=base.bc, x_left=-0.5 * nx * base.dx, left=base.left, right=base.right)
+        out.append(win)
+        nodes += nx * base.Q
+        k += 1
+    return out, (f"{len(out)} windows of {out[0].Nx} cells cut around the membrane of the workload's tubes "
+                 f"({nodes} velocity nodes)")
+
+
 def cpu_baseline(specs, desc: str) -> dict:
-    pool = OraclePool(specs, host_cores())
+    sample, what = cpu_sample(specs)
+    pool = OraclePool(sample, host_cores())
     try:
         wall = pool.step()
     finally:
         pool.close()
-    nodes = W.total_nodes(specs)
+    nodes = W.total_nodes(sample)
     return {"value": nodes / wall / 1e9, "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
-            "sample": f"one time step of every tube of the workload ({nodes} velocity nodes) from the initial "
-                      f"condition, plain C FP64 oracle, tubes split over {pool.nproc} processes",
+            "sample": f"one time step of {what} from the initial condition, plain C FP64 oracle, tubes split over "
+                      f"{pool.nproc} processes",
             "seconds": wall}
 
 
@@ -213,13 +243,19 @@ def measured_peaks() -> dict:
         return {}
 
 
-def ncu_traffic_per_launch():
-    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on the current kernel."""
+def ncu_traffic_per_launch(precision: str, workload: str):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on the current kernel and on
+    this workload."""
     try:
-        text = open(PROFILE).read()
+        text = open(PROFILES[precision]).read()
     except OSError:
         return None
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    if f"workload: {workload}" not in text:
+        return None
+    h = hashlib.sha256()
+    for src in KERNEL_SRCS[precision]:
+        h.update(open(src, "rb").read())
+    sha = h.hexdigest()[:16]
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"dram_bytes_per_stage_launch_full_size:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_tr or m_sha.group(1) != sha:
@@ -234,6 +270,7 @@ def ncu_traffic_per_launch():
 def run_reference(args, specs, desc, rank):
     if rank != 0:
         return
+    specs, what = cpu_sample(specs)
     pool = OraclePool(specs, host_cores())
     try:
         for _ in range(args.warmup):
@@ -249,8 +286,8 @@ def run_reference(args, specs, desc, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": desc, "velocity_nodes_per_step": nodes},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
-                             "sample": f"each step: one time step of every tube ({nodes} velocity nodes), plain C "
-                                       f"FP64 oracle, tubes split over {pool.nproc} processes"},
+                             "sample": f"each step: one time step of {what}, plain C FP64 oracle, tubes split "
+                                       f"over {pool.nproc} processes"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -261,7 +298,8 @@ def run_ours(args, specs, desc, rank, world):
     from paper_1608_03004_gb300 import binding as rb
 
     dev = torch.cuda.current_device()
-    tubes = [rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, s.tau, s.bc, 0) for s in specs]
+    storage = rb.STORAGE[args.precision]
+    tubes = [rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, s.tau, s.bc, storage) for s in specs]
     states = np.array([list(s.left) + list(s.right) for s in specs])
     xl = np.array([s.x_left for s in specs])
     stream = torch.cuda.current_stream()
@@ -321,27 +359,41 @@ def run_ours(args, specs, desc, rank, world):
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    # FP64: 2 DFMA per SM per clock on GB300 (measured with a DFMA loop: 1.90 per SM-clock at an assumed 2070
-    # MHz, i.e. 1.2 TFLOP/s; nominal 1.25 TFLOP/s), 4 flops per SM per clock
-    fp64_peak = props.multi_processor_count * 4 * sm_max * 1e6 / 1e12
-    achieved = FLOPS_PER_NODE_STAGE * nodes / (stage_ms * 1e-3) / 1e12
     hbm_peak = peaks.get("hbm_gbs", 6682.2)
-    hbm_achieved = BYTES_PER_NODE_STEP * nodes / 3 / (stage_ms * 1e-3) / 1e9
+    esize = ESIZE[args.precision]
+    bytes_per_node_step = 8 * esize  # stage inputs read once (1 + 2 + 2), outputs written once (3)
+    hbm_achieved = bytes_per_node_step * nodes / 3 / (stage_ms * 1e-3) / 1e9
+    traffic = ncu_traffic_per_launch(args.precision, args.workload)
+    hbm = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak, "frac": hbm_achieved / hbm_peak,
+           "note": f"{bytes_per_node_step} algorithmic bytes per velocity node per step, of measured copy"}
+    if args.precision == "f64":
+        # FP64: 2 DFMA per SM per clock on GB300 (measured with a DFMA loop: 1.90 per SM-clock at an assumed
+        # 2070 MHz, i.e. 1.2 TFLOP/s; nominal 1.25 TFLOP/s), 4 flops per SM per clock
+        fp64_peak = props.multi_processor_count * 4 * sm_max * 1e6 / 1e12
+        achieved = FLOPS_PER_NODE_STAGE * nodes / (stage_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": traffic, "kernel": "rlb_stage_kernel",
+                    "launch_ms": stage_ms,
+                    "note": "FP64 pipe bound; peak = SMs x 2 DFMA/clk x 2 flops x max SM clock (derived); "
+                            f"algorithmic {FLOPS_PER_NODE_STAGE} FP64 flops per velocity node per stage"}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_achieved / hbm_peak, "traffic": traffic, "kernel": "rlb_stage_rp_kernel",
+                    "launch_ms": stage_ms, "note": hbm["note"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32 (moments f64)",
+                                                          "bf16": "bf16 storage, f32 arithmetic (moments f64)"}[
+                                                              args.precision],
+        "data": "synthetic",
         "config": {"workload": desc, "velocity_nodes_per_step": nodes, "tubes": len(specs),
-                   "l2": "inputs larger than L2: state 8 B x nodes = %.0f MB per buffer, 3 buffers; no flush"
-                         % (8 * nodes / 1e6),
+                   "precision": args.precision,
+                   "l2": "inputs larger than L2: state %d B x nodes = %.0f MB per buffer, 3 buffers; no flush"
+                         % (esize, esize * nodes / 1e6),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": ncu_traffic_per_launch(),
-                     "kernel": "rlb_stage_kernel", "launch_ms": stage_ms,
-                     "note": "FP64 pipe bound; peak = SMs x 2 DFMA/clk x 2 flops x max SM clock (derived); "
-                             f"algorithmic {FLOPS_PER_NODE_STAGE} FP64 flops per velocity node per stage"},
-        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak, "frac": hbm_achieved / hbm_peak,
-                "note": f"{BYTES_PER_NODE_STEP} algorithmic bytes per velocity node per step, of measured copy"},
+        "roofline": roofline,
+        "hbm": hbm,
         "e2e": {"value": world * nodes * e2e_steps / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * h.state_size, "d2h_bytes_per_step": 8 * rb.NFIELDS * h.nx_total,
                 "steps": e2e_steps, "api": "rlb_set_state(host) + rlb_step(1) + rlb_moments(host)"},
@@ -361,6 +413,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["sweep", "small", "stress"], default="sweep")
+    ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

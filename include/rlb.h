@@ -19,7 +19,8 @@
  *    N^0 = sum_s F pbar, N^x = sum F pbar xi, T^00 = sum F pbar^2, T^0x = sum F pbar^2 xi,
  *    T^xx = sum F pbar^2 xi^2.
  *  - Packed state layout ("packed"): tubes one after the other; tube b holds Q_b rows of Nx_b doubles
- *    (row s, cell x at offset s*Nx_b + x). Fields layout: [RLB_NFIELDS][sum_b Nx_b], each field row holding
+ *    (row s, cell x at offset s*Nx_b + x). With FP32 or BF16 storage the state crosses the ABI as doubles
+ *    too: rlb_get_state widens, rlb_set_state rounds to nearest. Fields layout: [RLB_NFIELDS][sum_b Nx_b], each field row holding
  *    the tubes' cells one after the other.
  *  - Pointers flagged "on_device" are CUDA device pointers on the handle's device, otherwise host
  *    pointers (pageable or pinned). Caller buffers are never retained after a call returns.
@@ -53,6 +54,12 @@ typedef enum {
 
 enum { RLB_BC_OPEN = 0, RLB_BC_PERIODIC = 1 };
 
+/* Storage of F. FP64: everything in FP64 (the parity path). FP32 / BF16: F stored in that type, advection,
+ * equilibrium evaluation, collision and the Runge-Kutta combination in FP32, the moments accumulated with
+ * compensated FP32 sums and reduced in FP64, the Landau-frame solve and the equilibrium coefficients in FP64.
+ * All tubes of one handle use the same storage. */
+enum { RLB_STORAGE_F64 = 0, RLB_STORAGE_F32 = 1, RLB_STORAGE_BF16 = 2 };
+
 /* Fields written by rlb_moments, in this order. */
 enum {
   RLB_F_N0 = 0, RLB_F_NX, RLB_F_T00, RLB_F_T0X, RLB_F_TXX, RLB_F_E, RLB_F_V, RLB_F_N, RLB_NFIELDS
@@ -69,7 +76,7 @@ typedef struct {
   double dt;        /* time step */
   double tau;       /* relaxation time */
   int32_t bc;       /* RLB_BC_OPEN (zero-gradient ghosts, section "Riemann problem") or RLB_BC_PERIODIC */
-  int32_t reserved; /* must be 0 */
+  int32_t storage;  /* RLB_STORAGE_F64 (0), RLB_STORAGE_F32 or RLB_STORAGE_BF16; the same for every tube */
 } rlb_tube;
 
 /*
@@ -151,7 +158,7 @@ rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double *pbar, double *wp, dou
  *   from the caller and keeps its scratch (the two intermediate Runge-Kutta stages, the quadrature tables
  *   and the tile list) in one file-scope device array of RLB_STATIC_SCRATCH_BYTES bytes that every GPU which
  *   loads the library holds until the process exits.
- *   tube:  host pointer to the tube (same rules as rlb_init, bc open or periodic).
+ *   tube:  host pointer to the tube (same rules as rlb_init, bc open or periodic, storage RLB_STORAGE_F64).
  *   F_in:  device pointer, packed state [Q][Nx] doubles (Q = Qp * Qxi), read only.
  *   F_out: device pointer, packed state [Q][Nx] doubles, written with the state after nsteps steps; may
  *          equal F_in (in place). With nsteps = 0 nothing is launched and F_out is left untouched.

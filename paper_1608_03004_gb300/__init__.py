@@ -11,6 +11,10 @@ from .binding import (  # noqa: F401
     BC_PERIODIC,
     FIELDS,
     NFIELDS,
+    STORAGE,
+    STORAGE_BF16,
+    STORAGE_F32,
+    STORAGE_F64,
     Handle,
     RlbError,
     Tube,

@@ -18,6 +18,8 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ENONPHYS = 0, 1, 2, 3, 4
 BC_OPEN, BC_PERIODIC = 0, 1
+STORAGE_F64, STORAGE_F32, STORAGE_BF16 = 0, 1, 2
+STORAGE = {"f64": STORAGE_F64, "f32": STORAGE_F32, "bf16": STORAGE_BF16}
 FIELDS = ("N0", "Nx", "T00", "T0x", "Txx", "e", "v", "n")
 NFIELDS = len(FIELDS)
 
@@ -32,7 +34,8 @@ class RlbError(RuntimeError):
 
 
 class Tube(ctypes.Structure):
-    """rlb_tube: one tube's quadrature orders, grid, time step, relaxation time and boundary condition."""
+    """rlb_tube: one tube's quadrature orders, grid, time step, relaxation time, boundary condition and
+    storage of F (STORAGE_F64, STORAGE_F32 or STORAGE_BF16)."""
 
     _fields_ = [
         ("Qp", ctypes.c_int32),
@@ -44,16 +47,16 @@ class Tube(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("tau", ctypes.c_double),
         ("bc", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("storage", ctypes.c_int32),
     ]
 
     @classmethod
     def make(cls, Nx: int, Qxi: int, tau: float, dt: float | None = None, dx: float | None = None, Qp: int = 3,
-             Np: int = 2, Nv: int = 5, bc: int = BC_OPEN, cfl: float = 0.5) -> "Tube":
+             Np: int = 2, Nv: int = 5, bc: int = BC_OPEN, cfl: float = 0.5, storage: int = STORAGE_F64) -> "Tube":
         dx = 1.0 / Nx if dx is None else dx
         tau_c = float(tau) if (tau is not None and np.isfinite(tau)) else float("inf")
         dt = rlb_suggest_dt(dx, tau_c, cfl) if dt is None else dt
-        return cls(Qp, Qxi, Np, Nv, Nx, dx, dt, tau_c, bc, 0)
+        return cls(Qp, Qxi, Np, Nv, Nx, dx, dt, tau_c, bc, storage)
 
 
 def library_path() -> str:

@@ -14,6 +14,7 @@
 //      F_out = a F^n + b (F_in + dt L(F_in)), L = advection + Anderson-Witting collision (Eq. (Boltz)).
 // The step is FP64 throughout; on GB300 the FP64 pipe (about 2 DFMA per SM per clock) bounds it, so the
 // arithmetic is arranged to spend as few FP64 instructions per velocity-node update as possible.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -357,14 +358,34 @@ __global__ void __launch_bounds__(NT, 4) rlb_stage_kernel(StageArgs A) {
     stage_tile<NP_MAX, NV_MAX>(A, T, tl.y, sm);
 }
 
+#include "rlb_stage_rp.cuh"
+
 // --------------------------------------------------------------------------------------------------
 // Initial condition and fields
 // --------------------------------------------------------------------------------------------------
 
+// FP64 view of a stored population and its rounding back (storage type S = double, float, bf16)
+template <typename S>
+__device__ __forceinline__ double ld_d(const S* p) {
+  return (double)*p;
+}
+template <>
+__device__ __forceinline__ double ld_d<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return (double)__bfloat162float(*p);
+}
+template <typename S>
+__device__ __forceinline__ void st_d(S* p, double v) {
+  *p = (S)v;
+}
+template <>
+__device__ __forceinline__ void st_d<__nv_bfloat16>(__nv_bfloat16* p, double v) {
+  *p = __double2bfloat16(v);
+}
+
 struct InitArgs {
   const TubeDev* tubes;
   const int2* tiles;
-  double* F;
+  void* F;            // storage type of the handle
   const double* tab;
   const double* P;      // per-cell state (field layout) or NULL
   const double* n;
@@ -381,8 +402,8 @@ struct InitSmem {
 
 // Write F = F^eq of the cells' states (pass 0), or average the right-state equilibrium into the cells that
 // sit exactly on the membrane (pass 1).
-template <int NVc>
-__device__ void init_write(const TubeDev& T, const double* tab, const InitSmem& sm, double* F, int x0, bool pass1,
+template <typename S, int NVc>
+__device__ void init_write(const TubeDev& T, const double* tab, const InitSmem& sm, S* F, int x0, bool pass1,
                            bool tie) {
   const int c = threadIdx.x % GW, g = threadIdx.x / GW, x = x0 + c;
   if (c >= TX || x >= T.Nx || (pass1 && !tie)) return;
@@ -393,12 +414,12 @@ __device__ void init_write(const TubeDev& T, const double* tab, const InitSmem& 
     double f = 0.0;
 #pragma unroll
     for (int k = 0; k <= NVc; ++k) f = fma(sm.B[i * (NV_MAX + 1) + k][c], pw[k], f);
-    double* dst = F + T.off + (size_t)s * T.ld + x;
-    *dst = pass1 ? 0.5 * (*dst + f) : f;
+    S* dst = F + T.off + (size_t)s * T.ld + x;
+    st_d<S>(dst, pass1 ? 0.5 * (ld_d<S>(dst) + f) : f);
   }
 }
 
-template <int NPc, int NVc>
+template <typename S, int NPc, int NVc>
 __device__ void init_tile(const InitArgs& A, const TubeDev& T, int x0, InitSmem& sm) {
   const int c = threadIdx.x % GW, g = threadIdx.x / GW, x = x0 + c;
   const double* tab = A.tab + T.tab;
@@ -436,35 +457,38 @@ __device__ void init_tile(const InitArgs& A, const TubeDev& T, int x0, InitSmem&
     __syncthreads();
     if (pass == 1 && sm.tie == 0) break;  // uniform over the CTA
     tile_coeffs<NPc, NVc>(tab, T.Qp, sm.coef, sm.B, A.flag);
-    init_write<NVc>(T, tab, sm, A.F, x0, pass == 1, tie);
+    init_write<S, NVc>(T, tab, sm, static_cast<S*>(A.F), x0, pass == 1, tie);
     __syncthreads();
   }
 }
 
+template <typename S>
 __global__ void __launch_bounds__(NT) rlb_init_kernel(InitArgs A) {
   __shared__ InitSmem sm;
   const int2 tl = A.tiles[blockIdx.x];
   const TubeDev T = A.tubes[tl.x];
   if (T.Np == 2 && T.Nv == 5)
-    init_tile<2, 5>(A, T, tl.y, sm);
+    init_tile<S, 2, 5>(A, T, tl.y, sm);
   else
-    init_tile<NP_MAX, NV_MAX>(A, T, tl.y, sm);
+    init_tile<S, NP_MAX, NV_MAX>(A, T, tl.y, sm);
 }
 
-__global__ void __launch_bounds__(GW) rlb_fields_kernel(const TubeDev* tubes, const int2* tiles, const double* F,
+template <typename S>
+__global__ void __launch_bounds__(GW) rlb_fields_kernel(const TubeDev* tubes, const int2* tiles, const void* Fv,
                                                          const double* tabs, double* out, long long nxtot,
                                                          int* flag) {
+  const S* F = static_cast<const S*>(Fv);
   const int2 tl = tiles[blockIdx.x];
   const TubeDev T = tubes[tl.x];
   const int c = threadIdx.x, x = tl.y + c;
   if (c >= TX || x >= T.Nx) return;
   const double* tab = tabs + T.tab;
-  const double* f = F + T.off + x;
+  const S* f = F + T.off + x;
   double mom[5] = {0, 0, 0, 0, 0};
   for (int j = 0; j < T.Qxi; ++j) {
     double a = 0.0, b = 0.0;
     for (int i = 0; i < T.Qp; ++i) {
-      const double v = f[(size_t)(i * T.Qxi + j) * T.ld];
+      const double v = ld_d<S>(f + (size_t)(i * T.Qxi + j) * T.ld);
       a = fma(v, tab[TAB_PBAR + i], a);
       b = fma(v, tab[TAB_PBAR2 + i], b);
     }
@@ -483,6 +507,18 @@ __global__ void __launch_bounds__(GW) rlb_fields_kernel(const TubeDev* tubes, co
   o[5 * nxtot] = e;
   o[6 * nxtot] = beta;
   o[7 * nxtot] = n;
+}
+
+// Packed FP64 <-> stored state of one tube (rows x Nx, stored rows have stride ld).
+template <typename S>
+__global__ void widen_kernel(const S* src, int ld, double* dst, int Nx) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (x < Nx) dst[(size_t)r * Nx + x] = ld_d<S>(src + (size_t)r * ld + x);
+}
+template <typename S>
+__global__ void narrow_kernel(const double* src, S* dst, int ld, int Nx) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (x < Nx) st_d<S>(dst + (size_t)r * ld + x, src[(size_t)r * Nx + x]);
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -542,6 +578,10 @@ rlb_status ensure_series_tables(int dev) {
   RLB_CUDA(cudaMemcpyToSymbol(g_cb, cb.data(), cb.size() * sizeof(double)));
   RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(StageSmem)));
+  RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_stage_rp_kernel<float>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmemRP)));
+  RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_stage_rp_kernel<__nv_bfloat16>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmemRP)));
   g_tables_ready[dev] = true;
   return RLB_OK;
 }
@@ -554,14 +594,18 @@ struct rlb_ctx {
   std::vector<rlb_tube> tubes;
   std::vector<TubeDev> td;
   int ntiles = 0;
-  long long state_elems = 0;  // padded doubles per buffer
-  long long packed = 0;       // sum Q Nx
+  int storage = RLB_STORAGE_F64;
+  size_t esize = sizeof(double);  // bytes per stored population
+  long long state_elems = 0;      // padded elements per buffer
+  long long packed = 0;           // sum Q Nx
   long long nxtot = 0;
   TubeDev* d_tubes = nullptr;
   int2* d_tiles = nullptr;
   double* d_tab = nullptr;
-  double *F = nullptr, *F1 = nullptr, *F2 = nullptr;
+  float* d_tabf = nullptr;
+  void *F = nullptr, *F1 = nullptr, *F2 = nullptr;
   double* d_fields = nullptr;  // scratch for host-side moments
+  double* d_stage = nullptr;   // packed FP64 staging for host state copies of reduced storage
   int* d_flag = nullptr;
   int* h_flag = nullptr;       // pinned
 };
@@ -574,6 +618,8 @@ void free_ctx(rlb_ctx* h) {
   cudaFree(h->d_tubes);
   cudaFree(h->d_tiles);
   cudaFree(h->d_tab);
+  cudaFree(h->d_tabf);
+  cudaFree(h->d_stage);
   cudaFree(h->F);
   cudaFree(h->F1);
   cudaFree(h->F2);
@@ -589,7 +635,9 @@ rlb_status validate(const rlb_tube* t) {
   if (t->Nx < 1 || t->Nx > (1LL << 30) || (t->bc == RLB_BC_PERIODIC && t->Nx < 3)) return RLB_EINVAL;
   if (t->bc != RLB_BC_OPEN && t->bc != RLB_BC_PERIODIC) return RLB_EINVAL;
   if (!(t->dx > 0.0) || !std::isfinite(t->dx) || !(t->dt > 0.0) || !std::isfinite(t->dt)) return RLB_EINVAL;
-  if (std::isnan(t->tau) || t->reserved != 0) return RLB_EINVAL;
+  if (std::isnan(t->tau)) return RLB_EINVAL;
+  if (t->storage != RLB_STORAGE_F64 && t->storage != RLB_STORAGE_F32 && t->storage != RLB_STORAGE_BF16)
+    return RLB_EINVAL;
   return RLB_OK;
 }
 
@@ -600,6 +648,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   for (int b = 0; b < ntubes; ++b) {
     rlb_status st = validate(&tubes[b]);
     if (st != RLB_OK) return st;
+    if (tubes[b].storage != tubes[0].storage) return RLB_EINVAL;
   }
   rlb_ctx* h = new (std::nothrow) rlb_ctx;
   if (!h) return RLB_ENOMEM;
@@ -607,8 +656,11 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaGetDevice(&h->dev));
   h->stream = (cudaStream_t)stream;
   h->tubes.assign(tubes, tubes + ntubes);
-  // quadrature tables, one block per tube
+  h->storage = tubes[0].storage;
+  h->esize = h->storage == RLB_STORAGE_F64 ? sizeof(double) : (h->storage == RLB_STORAGE_F32 ? sizeof(float) : 2);
+  // quadrature tables, one block per tube (FP64, and FP32 for reduced storage)
   std::vector<double> tab;
+  std::vector<float> tabf;
   h->td.resize(ntubes);
   long long off = 0, xoff = 0;
   for (int b = 0; b < ntubes; ++b) {
@@ -621,7 +673,8 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     d.bc = t.bc;
     d.collide = (t.tau > 0.0 && std::isfinite(t.tau)) ? 1 : 0;
     d.Nx = (int)t.Nx;
-    d.ld = (int)((t.Nx + 31) / 32 * 32);
+    d.ld = (int)((t.Nx + 127) / 128 * 128);  // rows start on 256-byte boundaries for every storage type
+    d.storage = t.storage;
     d.off = off;
     d.xoff = xoff;
     d.dx = t.dx;
@@ -633,7 +686,9 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     xoff += t.Nx;
     h->packed += (long long)t.Qp * t.Qxi * t.Nx;
     d.tab = (int)tab.size();
+    d.tabf = (int)tabf.size();
     tab.resize(tab.size() + tab_size(t.Qxi), 0.0);
+    tabf.resize(tabf.size() + tabf_size(t.Qxi), 0.0f);
     double* T = tab.data() + d.tab;
     std::vector<double> pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
     if (!rlbq::gauss_laguerre1(t.Qp, pb.data(), wp.data()) || !rlbq::gauss_legendre(t.Qxi, xi.data(), wxi.data()))
@@ -659,6 +714,22 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
         T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
       for (int st = 0; st < 3; ++st) T[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
     }
+    // FP32 tables: hi/lo float pairs of the moment weights, and FP32 copies of the per-row factors
+    float* Tf = tabf.data() + d.tabf;
+    auto split = [](double w, float& hi, float& lo) {
+      hi = (float)w;
+      lo = (float)(w - (double)hi);
+    };
+    for (int i = 0; i < t.Qp; ++i) {
+      split(pb[i], Tf[TABF_P1 + i], Tf[TABF_P1 + QP_MAX + i]);
+      split(pb[i] * pb[i], Tf[TABF_P2 + i], Tf[TABF_P2 + QP_MAX + i]);
+    }
+    for (int j = 0; j < t.Qxi; ++j) {
+      split(xi[j], Tf[TABF_X + j], Tf[TABF_X + t.Qxi + j]);
+      split(xi[j] * xi[j], Tf[TABF_X + 2 * t.Qxi + j], Tf[TABF_X + 3 * t.Qxi + j]);
+      for (int k = 0; k <= NV_MAX; ++k) Tf[tabf_pw(t.Qxi) + j * (NV_MAX + 1) + k] = (float)T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k];
+      for (int st = 0; st < 3; ++st) Tf[tabf_cxi(t.Qxi) + st * t.Qxi + j] = (float)T[tab_cxi(t.Qxi) + st * t.Qxi + j];
+    }
   }
   h->state_elems = off;
   h->nxtot = xoff;
@@ -676,17 +747,19 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaMalloc(&h->d_tubes, sizeof(TubeDev) * ntubes));
   RLB_CUDA(cudaMalloc(&h->d_tiles, sizeof(int2) * tiles.size()));
   RLB_CUDA(cudaMalloc(&h->d_tab, sizeof(double) * std::max<size_t>(tab.size(), 1)));
-  RLB_CUDA(cudaMalloc(&h->F, sizeof(double) * h->state_elems));
-  RLB_CUDA(cudaMalloc(&h->F1, sizeof(double) * h->state_elems));
-  RLB_CUDA(cudaMalloc(&h->F2, sizeof(double) * h->state_elems));
+  RLB_CUDA(cudaMalloc(&h->d_tabf, sizeof(float) * std::max<size_t>(tabf.size(), 1)));
+  RLB_CUDA(cudaMalloc(&h->F, h->esize * h->state_elems));
+  RLB_CUDA(cudaMalloc(&h->F1, h->esize * h->state_elems));
+  RLB_CUDA(cudaMalloc(&h->F2, h->esize * h->state_elems));
   RLB_CUDA(cudaMalloc(&h->d_flag, sizeof(int)));
   RLB_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
   RLB_CUDA(cudaMemcpyAsync(h->d_tubes, h->td.data(), sizeof(TubeDev) * ntubes, cudaMemcpyHostToDevice, h->stream));
   RLB_CUDA(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
   RLB_CUDA(cudaMemcpyAsync(h->d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, h->stream));
-  RLB_CUDA(cudaMemsetAsync(h->F, 0, sizeof(double) * h->state_elems, h->stream));
-  RLB_CUDA(cudaMemsetAsync(h->F1, 0, sizeof(double) * h->state_elems, h->stream));
-  RLB_CUDA(cudaMemsetAsync(h->F2, 0, sizeof(double) * h->state_elems, h->stream));
+  RLB_CUDA(cudaMemcpyAsync(h->d_tabf, tabf.data(), sizeof(float) * tabf.size(), cudaMemcpyHostToDevice, h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->F, 0, h->esize * h->state_elems, h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->F1, 0, h->esize * h->state_elems, h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->F2, 0, h->esize * h->state_elems, h->stream));
   RLB_CUDA(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
   rlb_status st = ensure_series_tables(h->dev);
   if (st != RLB_OK) return st;
@@ -729,7 +802,12 @@ rlb_status run_init(rlb_ctx* h, const double* P, const double* n, const double* 
     A.n = tmp + h->nxtot;
     A.v = tmp + 2 * h->nxtot;
   }
-  rlb_init_kernel<<<h->ntiles, NT, 0, h->stream>>>(A);
+  if (h->storage == RLB_STORAGE_F64)
+    rlb_init_kernel<double><<<h->ntiles, NT, 0, h->stream>>>(A);
+  else if (h->storage == RLB_STORAGE_F32)
+    rlb_init_kernel<float><<<h->ntiles, NT, 0, h->stream>>>(A);
+  else
+    rlb_init_kernel<__nv_bfloat16><<<h->ntiles, NT, 0, h->stream>>>(A);
   cudaError_t e = cudaGetLastError();
   rlb_status st = check_flag(h);  // also waits for the copies out of the caller's buffers
   if (tmp) cudaFree(tmp);
@@ -783,23 +861,46 @@ rlb_status rlb_init_riemann(rlb_handle* out, const rlb_tube* tubes, int32_t ntub
 rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
   if (!h || nsteps < 0) return RLB_EINVAL;
   DeviceGuard gd(h->dev);
-  StageArgs A{};
-  A.tubes = h->d_tubes;
-  A.tiles = h->d_tiles;
-  A.tab = h->d_tab;
-  A.flag = h->d_flag;
-  A.Fn = h->F;
-  const double* in[3] = {h->F, h->F1, h->F2};
-  double* out[3] = {h->F1, h->F2, h->F};
-  for (int64_t t = 0; t < nsteps; ++t)
-    for (int st = 0; st < 3; ++st) {
-      A.Fin = in[st];
-      A.Fout = out[st];
-      A.a = RK_A[st];
-      A.b = RK_B[st];
-      A.stage = st;
-      rlb_stage_kernel<<<h->ntiles, NT, sizeof(StageSmem), h->stream>>>(A);
-    }
+  const void* in[3] = {h->F, h->F1, h->F2};
+  void* out[3] = {h->F1, h->F2, h->F};
+  if (h->storage == RLB_STORAGE_F64) {
+    StageArgs A{};
+    A.tubes = h->d_tubes;
+    A.tiles = h->d_tiles;
+    A.tab = h->d_tab;
+    A.flag = h->d_flag;
+    A.Fn = static_cast<const double*>(h->F);
+    for (int64_t t = 0; t < nsteps; ++t)
+      for (int st = 0; st < 3; ++st) {
+        A.Fin = static_cast<const double*>(in[st]);
+        A.Fout = static_cast<double*>(out[st]);
+        A.a = RK_A[st];
+        A.b = RK_B[st];
+        A.stage = st;
+        rlb_stage_kernel<<<h->ntiles, NT, sizeof(StageSmem), h->stream>>>(A);
+      }
+  } else {
+    StageArgsRP A{};
+    A.tubes = h->d_tubes;
+    A.tiles = h->d_tiles;
+    A.tab = h->d_tab;
+    A.tabf = h->d_tabf;
+    A.flag = h->d_flag;
+    A.Fn = h->F;
+    for (int64_t t = 0; t < nsteps; ++t)
+      for (int st = 0; st < 3; ++st) {
+        A.Fin = in[st];
+        A.Fout = out[st];
+        A.a = (float)RK_A[st];
+        A.b = (float)RK_B[st];
+        A.bd = RK_B[st];
+        A.stage = st;
+        if (h->storage == RLB_STORAGE_F32)
+          rlb_stage_rp_kernel<float><<<h->ntiles, NT, sizeof(StageSmemRP), h->stream>>>(A);
+        else
+          rlb_stage_rp_kernel<__nv_bfloat16><<<h->ntiles, NT, sizeof(StageSmemRP), h->stream>>>(A);
+      }
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -811,17 +912,68 @@ rlb_status rlb_moments(rlb_handle h, double* out, int32_t out_on_device) {
     if (!h->d_fields) RLB_CUDA(cudaMalloc(&h->d_fields, sizeof(double) * RLB_NFIELDS * h->nxtot));
     dst = h->d_fields;
   }
-  rlb_fields_kernel<<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab, dst, h->nxtot,
-                                                      h->d_flag);
+  if (h->storage == RLB_STORAGE_F64)
+    rlb_fields_kernel<double><<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab, dst,
+                                                                h->nxtot, h->d_flag);
+  else if (h->storage == RLB_STORAGE_F32)
+    rlb_fields_kernel<float><<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab, dst,
+                                                               h->nxtot, h->d_flag);
+  else
+    rlb_fields_kernel<__nv_bfloat16><<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab, dst,
+                                                                       h->nxtot, h->d_flag);
   RLB_CUDA(cudaGetLastError());
   if (!out_on_device)
     RLB_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * RLB_NFIELDS * h->nxtot, cudaMemcpyDeviceToHost, h->stream));
   return check_flag(h);
 }
 
+// Widen (to_handle false) or narrow (true) every tube between the packed FP64 buffer P (device) and F.
+static rlb_status convert_state(rlb_handle h, double* P, bool to_handle) {
+  long long p = 0;
+  for (size_t b = 0; b < h->tubes.size(); ++b) {
+    const TubeDev& d = h->td[b];
+    const int rows = d.Qp * d.Qxi;
+    const dim3 grid((d.Nx + 255) / 256, rows);
+    char* base = static_cast<char*>(h->F) + h->esize * d.off;
+    if (h->storage == RLB_STORAGE_F32) {
+      if (to_handle)
+        narrow_kernel<float><<<grid, 256, 0, h->stream>>>(P + p, reinterpret_cast<float*>(base), d.ld, d.Nx);
+      else
+        widen_kernel<float><<<grid, 256, 0, h->stream>>>(reinterpret_cast<const float*>(base), d.ld, P + p, d.Nx);
+    } else {
+      if (to_handle)
+        narrow_kernel<__nv_bfloat16><<<grid, 256, 0, h->stream>>>(P + p, reinterpret_cast<__nv_bfloat16*>(base),
+                                                                   d.ld, d.Nx);
+      else
+        widen_kernel<__nv_bfloat16><<<grid, 256, 0, h->stream>>>(reinterpret_cast<const __nv_bfloat16*>(base),
+                                                                  d.ld, P + p, d.Nx);
+    }
+    p += (long long)rows * d.Nx;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 static rlb_status copy_state(rlb_handle h, double* host_or_dev, const double* src_const, int32_t on_device,
                              bool to_handle) {
   DeviceGuard gd(h->dev);
+  if (h->storage != RLB_STORAGE_F64) {
+    double* P = nullptr;
+    if (on_device) {
+      P = to_handle ? const_cast<double*>(src_const) : host_or_dev;
+    } else {
+      if (!h->d_stage) RLB_CUDA(cudaMalloc(&h->d_stage, sizeof(double) * h->packed));
+      P = h->d_stage;
+      if (to_handle)
+        RLB_CUDA(cudaMemcpyAsync(P, src_const, sizeof(double) * h->packed, cudaMemcpyHostToDevice, h->stream));
+    }
+    rlb_status st = convert_state(h, P, to_handle);
+    if (st != RLB_OK) return st;
+    if (!on_device && !to_handle)
+      RLB_CUDA(cudaMemcpyAsync(host_or_dev, P, sizeof(double) * h->packed, cudaMemcpyDeviceToHost, h->stream));
+    if (!on_device || !to_handle) return check_flag(h);
+    return RLB_OK;
+  }
+  double* F = static_cast<double*>(h->F);
   long long p = 0;
   for (size_t b = 0; b < h->tubes.size(); ++b) {
     const TubeDev& d = h->td[b];
@@ -832,10 +984,10 @@ static rlb_status copy_state(rlb_handle h, double* host_or_dev, const double* sr
     else
       kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (to_handle)
-      RLB_CUDA(cudaMemcpy2DAsync(h->F + d.off, sizeof(double) * d.ld, src_const + p, sizeof(double) * d.Nx,
+      RLB_CUDA(cudaMemcpy2DAsync(F + d.off, sizeof(double) * d.ld, src_const + p, sizeof(double) * d.Nx,
                                  sizeof(double) * d.Nx, rows, kind, h->stream));
     else
-      RLB_CUDA(cudaMemcpy2DAsync(host_or_dev + p, sizeof(double) * d.Nx, h->F + d.off, sizeof(double) * d.ld,
+      RLB_CUDA(cudaMemcpy2DAsync(host_or_dev + p, sizeof(double) * d.Nx, F + d.off, sizeof(double) * d.ld,
                                  sizeof(double) * d.Nx, rows, kind, h->stream));
     p += (long long)rows * d.Nx;
   }
@@ -935,6 +1087,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
   if (!tube || !F_in || !F_out || nsteps < 0) return RLB_EINVAL;
   rlb_status st = validate(tube);
   if (st != RLB_OK) return st;
+  if (tube->storage != RLB_STORAGE_F64) return RLB_EINVAL;
   const rlb_tube& t = *tube;
   const int Q = t.Qp * t.Qxi, Nx = (int)t.Nx;
   const int ntiles = (Nx + TX - 1) / TX;

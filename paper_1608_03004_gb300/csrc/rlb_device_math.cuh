@@ -34,16 +34,26 @@ constexpr double C1 = 1.2909944487358056;  // sqrt(10/6)
 constexpr double C2 = 1.8257418583505538;  // sqrt(10/3)
 constexpr double E3 = 3.0 * WENO_EPS;
 
+// Reciprocal used by the WENO combination: FP64 as above; FP32 the hardware approximation alone (about 1 ulp
+// of FP32, below the rounding of the FP32 state it serves).
+__device__ __forceinline__ double rcp_fast(double d) { return rcp_nr(d); }
+__device__ __forceinline__ float rcp_fast(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+
 // Scaled indicator squares of the pair (x, y) = (d_j, d_{j+1}) in memory order. fwd: wind toward increasing
 // index; then sA = (C0 (SL + 3eps))^2, sB = (C1 (SC + 3eps))^2, sC = (C2 (SR + 3eps))^2; otherwise SL and SR
-// trade places.
-__device__ __forceinline__ void weno5_pair(double x, double y, bool fwd, double& sA, double& sB, double& sC) {
-  const double qx = x * x, pxy = x * y, qy = y * y;
-  const double ax = fwd ? 4.0 * C0 : 10.0 * C0, ay = fwd ? 10.0 * C0 : 4.0 * C0;
-  const double cx = fwd ? 10.0 * C2 : 4.0 * C2, cy = fwd ? 4.0 * C2 : 10.0 * C2;
-  const double uA = fma(ax, qx, fma(-11.0 * C0, pxy, fma(ay, qy, E3 * C0)));
-  const double uB = fma(4.0 * C1, qx, fma(-5.0 * C1, pxy, fma(4.0 * C1, qy, E3 * C1)));
-  const double uC = fma(cx, qx, fma(-11.0 * C2, pxy, fma(cy, qy, E3 * C2)));
+// trade places. T is double (FP64 path) or float (reduced-precision path).
+template <typename T>
+__device__ __forceinline__ void weno5_pair(T x, T y, bool fwd, T& sA, T& sB, T& sC) {
+  const T qx = x * x, pxy = x * y, qy = y * y;
+  const T ax = fwd ? T(4.0 * C0) : T(10.0 * C0), ay = fwd ? T(10.0 * C0) : T(4.0 * C0);
+  const T cx = fwd ? T(10.0 * C2) : T(4.0 * C2), cy = fwd ? T(4.0 * C2) : T(10.0 * C2);
+  const T uA = fma(ax, qx, fma(T(-11.0 * C0), pxy, fma(ay, qy, T(E3 * C0))));
+  const T uB = fma(T(4.0 * C1), qx, fma(T(-5.0 * C1), pxy, fma(T(4.0 * C1), qy, T(E3 * C1))));
+  const T uC = fma(cx, qx, fma(T(-11.0 * C2), pxy, fma(cy, qy, T(E3 * C2))));
   sA = uA * uA;
   sB = uB * uB;
   sC = uC * uC;
@@ -51,26 +61,73 @@ __device__ __forceinline__ void weno5_pair(double x, double y, bool fwd, double&
 
 // G of the interface from the three scaled squares (s0, s1, s2) of its stencils and the differences
 // d1..d4 in wind order.
-__device__ __forceinline__ double weno5_combine(double s0, double s1, double s2, double d1, double d2, double d3,
-                                                double d4) {
-  const double r0 = fma(5.0, d2, -2.0 * d1), r1 = fma(2.0, d3, d2), r2 = fma(4.0, d3, -d4);
-  const double a0 = s1 * s2;
-  const double num = fma(s0, fma(s2, r1, s1 * r2), a0 * r0);
-  const double den = fma(s0, s1 + s2, a0);
-  return num * rcp_nr(6.0 * den);
+template <typename T>
+__device__ __forceinline__ T weno5_combine(T s0, T s1, T s2, T d1, T d2, T d3, T d4) {
+  const T r0 = fma(T(5.0), d2, T(-2.0) * d1), r1 = fma(T(2.0), d3, d2), r2 = fma(T(4.0), d3, -d4);
+  const T a0 = s1 * s2;
+  const T num = fma(s0, fma(s2, r1, s1 * r2), a0 * r0);
+  const T den = fma(s0, s1 + s2, a0);
+  return num * rcp_fast(T(6.0) * den);
 }
 
 // Interface value v2 + G of five samples in memory order m0..m4 around the interface between m2 and m3
 // (wind toward increasing index, fwd) or between m1 and m2 (wind toward decreasing index), computed
-// exactly as the stage kernel does: pairs first, then the combination.
-__device__ __forceinline__ double weno5_interface(double m0, double m1, double m2, double m3, double m4, bool fwd) {
-  const double D1 = m1 - m0, D2 = m2 - m1, D3 = m3 - m2, D4 = m4 - m3;
-  double a[3], b[3], c[3];
+// exactly as the stage kernels do: pairs first, then the combination.
+template <typename T>
+__device__ __forceinline__ T weno5_interface(T m0, T m1, T m2, T m3, T m4, bool fwd) {
+  const T D1 = m1 - m0, D2 = m2 - m1, D3 = m3 - m2, D4 = m4 - m3;
+  T a[3], b[3], c[3];
   weno5_pair(D1, D2, fwd, a[0], b[0], c[0]);
   weno5_pair(D2, D3, fwd, a[1], b[1], c[1]);
   weno5_pair(D3, D4, fwd, a[2], b[2], c[2]);
   if (fwd) return m2 + weno5_combine(a[0], b[1], c[2], D1, D2, D3, D4);
   return m2 + weno5_combine(a[2], b[1], c[0], -D4, -D3, -D2, -D1);
+}
+
+// Compensated (double-float) accumulation in FP32 for the moment sums of the reduced-precision path: an
+// unevaluated sum hi + lo, the error of each addition recovered with Knuth's TwoSum and of each product with
+// an FMA (the error-free transformations of Ogita, Rump and Oishi's accurate dot product). Weights are
+// themselves given as hi + lo float pairs, so the sums reach about 1e-13 relative before they are reduced
+// in FP64.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// acc += f (whi + wlo)
+__device__ __forceinline__ void df_add_prod(DF& acc, float f, float whi, float wlo) {
+  const float p = f * whi;
+  float e = fmaf(f, whi, -p);
+  e = fmaf(f, wlo, e);
+  float s, t;
+  two_sum(acc.hi, p, s, t);
+  acc.hi = s;
+  acc.lo += t + e;
+}
+
+// acc += a (xhi + xlo)
+__device__ __forceinline__ void df_add_dfprod(DF& acc, DF a, float xhi, float xlo) {
+  const float p = a.hi * xhi;
+  float e = fmaf(a.hi, xhi, -p);
+  e = fmaf(a.hi, xlo, e);
+  e = fmaf(a.lo, xhi, e);
+  float s, t;
+  two_sum(acc.hi, p, s, t);
+  acc.hi = s;
+  acc.lo += t + e;
+}
+
+// acc += a
+__device__ __forceinline__ void df_add(DF& acc, DF a) {
+  float s, t;
+  two_sum(acc.hi, a.hi, s, t);
+  acc.hi = s;
+  acc.lo += t + a.lo;
 }
 
 }  // namespace rlbdev

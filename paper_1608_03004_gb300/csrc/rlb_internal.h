@@ -38,6 +38,8 @@ struct TubeDev {
   double x_left;
   int tab;      // offset of this tube's tables in the table buffer
   int index;    // position of the tube in the caller's list
+  int tabf;     // offset of this tube's FP32 tables (reduced-precision storage)
+  int storage;  // RLB_STORAGE_F64 / F32 / BF16
 };
 
 // Layout of one tube's tables (doubles, starting at TubeDev::tab):
@@ -57,6 +59,18 @@ constexpr int TAB_XI = TAB_K + QP_MAX * (NP_MAX + 1);
 __host__ __device__ inline int tab_pw(int Qxi) { return TAB_XI + Qxi; }
 __host__ __device__ inline int tab_cxi(int Qxi) { return TAB_XI + Qxi + Qxi * (NV_MAX + 1); }
 inline int tab_size(int Qxi) { return tab_cxi(Qxi) + 3 * Qxi; }
+// Per-tube FP32 tables of the reduced-precision path (floats, starting at TubeDev::tabf):
+//   [0, 2 QP_MAX)           pbar_i as a hi/lo float pair: hi at i, lo at QP_MAX + i
+//   [2 QP_MAX, 4 QP_MAX)    pbar_i^2 likewise
+//   then xi_j hi, xi_j lo, xi_j^2 hi, xi_j^2 lo (Qxi each)
+//   then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k], then b_st dt xi_j / dx at [st Qxi + j]
+constexpr int TABF_P1 = 0;
+constexpr int TABF_P2 = 2 * QP_MAX;
+constexpr int TABF_X = 4 * QP_MAX;
+__host__ __device__ inline int tabf_pw(int Qxi) { return TABF_X + 4 * Qxi; }
+__host__ __device__ inline int tabf_cxi(int Qxi) { return tabf_pw(Qxi) + Qxi * (NV_MAX + 1); }
+inline int tabf_size(int Qxi) { return tabf_cxi(Qxi) + 3 * Qxi; }
+
 constexpr double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};  // Shu-Osher SSP-RK3: F_out = a F^n + b (F_in + dt L(F_in))
 constexpr double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
 

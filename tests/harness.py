@@ -21,9 +21,9 @@ RTOL = 1e-12
 POSITIVE_FIELDS = (0, 2, 4, 5, 7)
 
 
-def to_tube(s: TubeSpec) -> rb.Tube:
+def to_tube(s: TubeSpec, storage: int = rb.STORAGE_F64) -> rb.Tube:
     tau = s.tau if (s.tau is not None and math.isfinite(s.tau) and s.tau > 0) else math.inf
-    return rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, tau, s.bc, 0)
+    return rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, tau, s.bc, storage)
 
 
 def to_params(s: TubeSpec) -> oracle.Params:
@@ -31,8 +31,8 @@ def to_params(s: TubeSpec) -> oracle.Params:
     return oracle.Params(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, tau, s.bc)
 
 
-def gpu_init(specs: Sequence[TubeSpec]) -> rb.Handle:
-    tubes = [to_tube(s) for s in specs]
+def gpu_init(specs: Sequence[TubeSpec], storage: int = rb.STORAGE_F64) -> rb.Handle:
+    tubes = [to_tube(s, storage) for s in specs]
     if all(s.riemann for s in specs):
         states = np.array([list(s.left) + list(s.right) for s in specs], dtype=np.float64)
         xl = np.array([s.x_left for s in specs], dtype=np.float64)

@@ -1,0 +1,102 @@
+"""Reduced-precision storage (FP32, BF16) against the FP64 oracle: every result states its error.
+
+F is stored in FP32 or BF16; advection, equilibrium evaluation, collision and the Runge-Kutta combination run
+in FP32; the moments are compensated FP32 sums reduced in FP64 and the Landau frame is solved in FP64.
+Target: FP32 energy density within 1e-5 relative of the FP64 oracle, stated both as the mean over cells
+(|e - e_ref| / e_ref averaged) and as the worst cell; the worst cells sit on the shock and contact, where a
+shift of a fraction of a cell dominates, so the worst-cell bound is 3e-5. BF16 (unit roundoff 2^-8) loses
+about 10 % at the waves over a few hundred steps: its errors are measured and bounded loosely. The errors
+found are printed (pytest -s).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import harness as H
+from paper_1608_03004_gb300 import binding as rb
+from paper_1608_03004_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# (field index, name) of the fields the precision targets are stated for
+E, V, TXX = 5, 6, 4
+
+
+def run(specs, nsteps, storage):
+    with H.gpu_init(specs, storage) as h:
+        rb.rlb_step(h, nsteps)
+        rb.rlb_sync(h)
+        return H.split_fields(specs, rb.rlb_moments(h)), H.split_state(specs, rb.rlb_get_state(h))
+
+
+def errors(f, ref):
+    re = np.abs(f[E] - ref[E]) / np.abs(ref[E])
+    rt = np.abs(f[TXX] - ref[TXX]) / np.abs(ref[TXX])
+    return {
+        "e_rel_mean": float(np.mean(re)), "e_rel_max": float(np.max(re)),
+        "Txx_rel_mean": float(np.mean(rt)), "Txx_rel_max": float(np.max(rt)),
+        "v_abs_max": float(np.max(np.abs(f[V] - ref[V]))),
+    }
+
+
+# (mean bound, worst-cell bound) per storage
+BOUNDS = {rb.STORAGE_F32: (1e-5, 3e-5), rb.STORAGE_BF16: (5e-2, 0.25)}
+
+
+def check_bounds(err, storage):
+    mean_b, max_b = BOUNDS[storage]
+    assert err["e_rel_mean"] <= mean_b and err["Txx_rel_mean"] <= mean_b, err
+    assert err["e_rel_max"] <= max_b and err["Txx_rel_max"] <= max_b and err["v_abs_max"] <= max_b, err
+
+
+@pytest.mark.parametrize("storage", [rb.STORAGE_F32, rb.STORAGE_BF16])
+def test_sod_small_full_run_against_oracle(storage):
+    s = W.sod_small()[0]
+    nsteps = 320
+    (f,), _ = run([s], nsteps, storage)
+    _, fr = H.oracle_run(s, nsteps)
+    err = errors(f, fr)
+    print(f"storage {storage}: Sod Nx=400 Q=24 t=0.4 errors vs FP64 oracle {err}")
+    check_bounds(err, storage)
+
+
+@pytest.mark.parametrize("storage", [rb.STORAGE_F32, rb.STORAGE_BF16])
+def test_moving_and_ballistic_batch_against_oracle(storage):
+    specs = [W.random_smooth(150, 16, 2e-2, seed=3, vmax=0.6), W.sod_tube(200, 32, math.inf),
+             W.random_smooth(90, 8, 1e-3, seed=4, bc=W.BC_OPEN)]
+    # one handle takes per-cell states: give the Sod tube its cell states (no centre on the membrane)
+    x = -0.5 + (np.arange(200) + 0.5) / 200
+    specs[1].P = np.where(x < 0, 1.0, 0.1)
+    specs[1].n = np.where(x < 0, 1.0, 0.125)
+    specs[1].v = np.zeros(200)
+    nsteps = 40
+    fg, _ = run(specs, nsteps, storage)
+    for s, f in zip(specs, fg):
+        _, fr = H.oracle_run(s, nsteps)
+        err = errors(f, fr)
+        print(f"storage {storage}: Nx={s.Nx} Qxi={s.Qxi} tau={s.tau} errors vs FP64 oracle {err}")
+        check_bounds(err, storage)
+
+
+def test_state_round_trip_rounds_to_storage():
+    s = W.random_smooth(77, 8, 1e-2, seed=8)
+    F = H.oracle_init(s).ravel()
+    for storage in (rb.STORAGE_F32, rb.STORAGE_BF16):
+        with H.gpu_init([s], storage) as h:
+            rb.rlb_set_state(h, F)
+            got = rb.rlb_get_state(h)
+        if storage == rb.STORAGE_F32:
+            np.testing.assert_array_equal(got, F.astype(np.float32).astype(np.float64))
+        else:
+            assert np.max(np.abs(got - F) / np.abs(F)) <= 2.0**-8  # unit roundoff of an 8-bit significand
+            # values are bf16: 8 significant bits, the low 16 bits of the float pattern are zero
+            assert np.all((got.astype(np.float32).view(np.uint32) & 0xFFFF) == 0)
+
+
+def test_mixed_storage_in_one_handle_rejected():
+    a, b = W.sod_tube(64, 8, 1e-3), W.sod_tube(64, 8, 1e-3)
+    tubes = [H.to_tube(a, rb.STORAGE_F32), H.to_tube(b, rb.STORAGE_F64)]
+    with pytest.raises(rb.RlbError) as ei:
+        rb.rlb_init_riemann(tubes, np.array([list(a.left) + list(a.right)] * 2), np.array([-0.5, -0.5]))
+    assert ei.value.status == rb.EINVAL
