@@ -57,14 +57,15 @@ ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
 CPU_SAMPLE_NODES = 24_000_000  # bound on the velocity nodes the oracle advances per CPU sample step
 
 
-def workload(name: str):
+def workload(name: str, nx: int | None = None):
     if name == "sweep":
         return W.sod_sweep(), ("Sod tube sweep: Nx=4096, tau in {1e-4,1e-3,1e-2,1e-1,1,10,inf} x Qxi in "
                                "{8,32,128,200}, Qp=3, Np=2, Nv=5, CFL 0.5 (dt=min(0.5dx,1.25tau)), open BC")
     if name == "small":
         return W.sod_small(), "Sod tube: Nx=400, Qp=3, Qxi=8, tau=1e-3, CFL 0.5, open BC"
     if name == "stress":
-        return [W.stress()], "Sod tube: Nx=1048576, Qp=3, Qxi=128, tau=1e-2, CFL 0.5, open BC"
+        n = nx or (1 << 20)
+        return [W.stress(Nx=n)], f"Sod tube: Nx={n}, Qp=3, Qxi=128, tau=1e-2, CFL 0.5, open BC"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -250,7 +251,7 @@ def ncu_traffic_per_launch(precision: str, workload: str):
         text = open(PROFILES[precision]).read()
     except OSError:
         return None
-    if f"workload: {workload}" not in text:
+    if f"workload: {workload}" not in text:  # the profile names the workload it was captured on
         return None
     h = hashlib.sha256()
     for src in KERNEL_SRCS[precision]:
@@ -363,7 +364,7 @@ def run_ours(args, specs, desc, rank, world):
     esize = ESIZE[args.precision]
     bytes_per_node_step = 8 * esize  # stage inputs read once (1 + 2 + 2), outputs written once (3)
     hbm_achieved = bytes_per_node_step * nodes / 3 / (stage_ms * 1e-3) / 1e9
-    traffic = ncu_traffic_per_launch(args.precision, args.workload)
+    traffic = ncu_traffic_per_launch(args.precision, args.workload) if args.nx is None else None
     hbm = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak, "frac": hbm_achieved / hbm_peak,
            "note": f"{bytes_per_node_step} algorithmic bytes per velocity node per step, of measured copy"}
     if args.precision == "f64":
@@ -414,11 +415,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["sweep", "small", "stress"], default="sweep")
     ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default="f64")
+    ap.add_argument("--nx", type=int, default=None, help="cells of the stress tube (default 1048576)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    specs, desc = workload(args.workload)
+    specs, desc = workload(args.workload, args.nx)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -606,6 +606,8 @@ struct rlb_ctx {
   void *F = nullptr, *F1 = nullptr, *F2 = nullptr;
   double* d_fields = nullptr;  // scratch for host-side moments
   double* d_stage = nullptr;   // packed FP64 staging for host state copies of reduced storage
+  double *M = nullptr, *M1 = nullptr, *M2 = nullptr;  // reduced storage: FP64 moments of F, F1, F2
+                                                       // ([RLB_NFIELDS][nxtot]; the first 5 rows are used)
   int* d_flag = nullptr;
   int* h_flag = nullptr;       // pinned
 };
@@ -620,6 +622,9 @@ void free_ctx(rlb_ctx* h) {
   cudaFree(h->d_tab);
   cudaFree(h->d_tabf);
   cudaFree(h->d_stage);
+  cudaFree(h->M);
+  cudaFree(h->M1);
+  cudaFree(h->M2);
   cudaFree(h->F);
   cudaFree(h->F1);
   cudaFree(h->F2);
@@ -753,6 +758,11 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaMalloc(&h->F2, h->esize * h->state_elems));
   RLB_CUDA(cudaMalloc(&h->d_flag, sizeof(int)));
   RLB_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
+  if (h->storage != RLB_STORAGE_F64) {
+    RLB_CUDA(cudaMalloc(&h->M, sizeof(double) * RLB_NFIELDS * h->nxtot));
+    RLB_CUDA(cudaMalloc(&h->M1, sizeof(double) * RLB_NFIELDS * h->nxtot));
+    RLB_CUDA(cudaMalloc(&h->M2, sizeof(double) * RLB_NFIELDS * h->nxtot));
+  }
   RLB_CUDA(cudaMemcpyAsync(h->d_tubes, h->td.data(), sizeof(TubeDev) * ntubes, cudaMemcpyHostToDevice, h->stream));
   RLB_CUDA(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
   RLB_CUDA(cudaMemcpyAsync(h->d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, h->stream));
@@ -774,6 +784,18 @@ rlb_status check_flag(rlb_ctx* h) {
     return RLB_ENONPHYS;
   }
   return RLB_OK;
+}
+
+// Reduced storage: the stage kernel reads the moments of its input from M; recompute them (FP64) whenever F is
+// written from outside the step (initial condition, rlb_set_state).
+rlb_status refresh_moments(rlb_ctx* h) {
+  if (h->storage == RLB_STORAGE_F32)
+    rlb_fields_kernel<float><<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab, h->M,
+                                                               h->nxtot, h->d_flag);
+  else if (h->storage == RLB_STORAGE_BF16)
+    rlb_fields_kernel<__nv_bfloat16><<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab,
+                                                                       h->M, h->nxtot, h->d_flag);
+  return cuda_status(cudaGetLastError());
 }
 
 rlb_status run_init(rlb_ctx* h, const double* P, const double* n, const double* v, int on_device,
@@ -809,6 +831,10 @@ rlb_status run_init(rlb_ctx* h, const double* P, const double* n, const double* 
   else
     rlb_init_kernel<__nv_bfloat16><<<h->ntiles, NT, 0, h->stream>>>(A);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && h->storage != RLB_STORAGE_F64) {
+    const rlb_status sm = refresh_moments(h);
+    if (sm != RLB_OK) return sm;
+  }
   rlb_status st = check_flag(h);  // also waits for the copies out of the caller's buffers
   if (tmp) cudaFree(tmp);
   if (e != cudaSuccess) return cuda_status(e);
@@ -887,10 +913,15 @@ rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
     A.tabf = h->d_tabf;
     A.flag = h->d_flag;
     A.Fn = h->F;
+    A.nxtot = h->nxtot;
+    const double* min[3] = {h->M, h->M1, h->M2};
+    double* mout[3] = {h->M1, h->M2, h->M};
     for (int64_t t = 0; t < nsteps; ++t)
       for (int st = 0; st < 3; ++st) {
         A.Fin = in[st];
         A.Fout = out[st];
+        A.Min = min[st];
+        A.Mout = mout[st];
         A.a = (float)RK_A[st];
         A.b = (float)RK_B[st];
         A.bd = RK_B[st];
@@ -967,6 +998,7 @@ static rlb_status copy_state(rlb_handle h, double* host_or_dev, const double* sr
         RLB_CUDA(cudaMemcpyAsync(P, src_const, sizeof(double) * h->packed, cudaMemcpyHostToDevice, h->stream));
     }
     rlb_status st = convert_state(h, P, to_handle);
+    if (st == RLB_OK && to_handle) st = refresh_moments(h);
     if (st != RLB_OK) return st;
     if (!on_device && !to_handle)
       RLB_CUDA(cudaMemcpyAsync(host_or_dev, P, sizeof(double) * h->packed, cudaMemcpyDeviceToHost, h->stream));
