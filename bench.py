@@ -60,7 +60,7 @@ CPU_SAMPLE_NODES = 24_000_000  # bound on the velocity nodes the oracle advances
 def workload(name: str, nx: int | None = None):
     if name == "sweep":
         return W.sod_sweep(), ("Sod tube sweep: Nx=4096, tau in {1e-4,1e-3,1e-2,1e-1,1,10,inf} x Qxi in "
-                               "{8,32,128,200}, Qp=3, Np=2, Nv=5, CFL 0.5 (dt=min(0.5dx,1.25tau)), open BC")
+                               "{8,32,128,200}, Qp=3, Np=2, Nv=5, CFL 0.5 (dt=min(0.5dx,0.9tau)), open BC")
     if name == "small":
         return W.sod_small(), "Sod tube: Nx=400, Qp=3, Qxi=8, tau=1e-3, CFL 0.5, open BC"
     if name == "stress":

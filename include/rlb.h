@@ -134,10 +134,11 @@ int64_t rlb_state_size(rlb_handle h);
 const char *rlb_error_string(rlb_status s);
 
 /*
- * rlb_suggest_dt - time step min(cfl * dx, 1.25 tau): the CFL bound for particle speeds |xi| <= 1 (the
+ * rlb_suggest_dt - time step min(cfl * dx, 0.9 tau): the CFL bound for particle speeds |xi| <= 1 (the
  *   paper bounds its step by the CFL condition in section "Numerical results"; cfl = 0.5 gives its
- *   dt = 0.5e-4 at dx = 1e-4) and the SSP-RK3 stability limit of the stiff collision term for |v| <= 0.6.
- *   tau <= 0 or infinite: cfl * dx.
+ *   dt = 0.5e-4 at dx = 1e-4) and the stiffness bound of SSP-RK3 with WENO5 advection: at cfl <= 0.5 the
+ *   step is stable while dt gamma (1 + |v|) / tau <= 1.977 (linear analysis), i.e. up to |v| ~ 0.63 with
+ *   0.9 tau. Faster flows need a smaller dt. tau <= 0 or infinite: cfl * dx.
  */
 double rlb_suggest_dt(double dx, double tau, double cfl);
 

@@ -152,9 +152,12 @@ def weno5(vm2, vm1, v0, vp1, vp2) -> float:
 
 
 def params(Qp=3, Qxi=8, Np=2, Nv=5, Nx=400, dx=None, dt=None, tau=1e-3, bc=BC_OPEN) -> Params:
+    """Run parameters; the default time step is min(0.5 dx, 0.9 tau), the stable rule for SSP-RK3 with WENO5
+    advection and stiff relaxation at |v| <= 0.63 (tests/test_stability.py)."""
     dx = 1.0 / Nx if dx is None else dx
-    dt = 0.5 * dx if dt is None else dt
     tau = 0.0 if (tau is None or not np.isfinite(tau)) else tau
+    if dt is None:
+        dt = 0.5 * dx if tau <= 0 else min(0.5 * dx, 0.9 * tau)
     return Params(Qp, Qxi, Np, Nv, Nx, dx, dt, tau, bc)
 
 

@@ -1068,7 +1068,7 @@ const char* rlb_error_string(rlb_status s) {
 
 double rlb_suggest_dt(double dx, double tau, double cfl) {
   double dt = cfl * dx;
-  if (tau > 0.0 && std::isfinite(tau)) dt = std::min(dt, 1.25 * tau);
+  if (tau > 0.0 && std::isfinite(tau)) dt = std::min(dt, 0.9 * tau);
   return dt;
 }
 

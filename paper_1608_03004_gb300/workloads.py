@@ -6,12 +6,14 @@ condition, either Riemann data (left/right states of Eq. (condinit), section "Ri
 
 Workloads (sizes as stated):
   * ``sod_small``: the paper's Sod tube (P, n, v) = (1, 1, 0) | (0.1, 0.125, 0) on x in [-0.5, 0.5],
-    Nx = 400, Qp = 3, Qxi = 8 (24 velocities), tau = 1e-3, CFL 0.5 (dt = 1.25e-3, 320 steps to t = 0.4).
+    Nx = 400, Qp = 3, Qxi = 8 (24 velocities), tau = 1e-3, CFL 0.5 (dt = min(1.25e-3, 0.9 tau) = 9e-4,
+    444 steps to t = 0.4).
   * ``sod_sweep``: the relaxation-time sweep, Nx = 4096, tau in {1e-4, 1e-3, 1e-2, 1e-1, 1, 10, inf} x
-    Qxi in {8, 32, 128, 200}, Qp = 3: 28 tubes, 31.65 M velocity nodes; dt = min(0.5 dx, 1.25 tau).
+    Qxi in {8, 32, 128, 200}, Qp = 3: 28 tubes, 31.65 M velocity nodes; dt = min(0.5 dx, 0.9 tau).
   * ``batched_tubes``: 256 tubes, seed 160803004: Nx ~ U[1024, 16384], log10 tau ~ U[-4, 1],
     Qxi in {8, 16, 32, 64}, P_L ~ U[0.5, 2], P_R = P_L U(0.01, 0.5), n_L = P_L, n_R = P_R / 0.8 (the paper
-    is silent on n; this keeps its T_L = 1, T_R = 0.8 and reproduces (1, 0.125) at P = (1, 0.1)).
+    is silent on n; this keeps its T_L = 1, T_R = 0.8 and reproduces (1, 0.125) at P = (1, 0.1));
+    dt = min(0.5 dx, 0.45 tau) (the strong shocks reach |v| ~ 0.8).
   * ``gaussian_bumps``: Nx = 2048, Qxi = 32, per-cell pressure 1 + sum of seed-fixed Gaussian bumps of
     relative amplitude 0.05, n = P, v = 0.
   * ``stress``: one Sod tube, Nx = 1,048,576, Qxi = 128 (384 velocities), tau = 1e-2.
@@ -60,19 +62,24 @@ class TubeSpec:
         return self.P is None
 
 
-def cfl_dt(dx: float, tau: float, cfl: float = 0.5) -> float:
-    """Time step rule of the workloads: min(cfl dx, 1.25 tau) (1.25 tau keeps SSP-RK3 stable for |v| <= 0.6)."""
+STIFF_SOD = 0.9     # dt <= 0.9 tau: SSP-RK3 + WENO5 at CFL 0.5 stays stable up to |v| ~ 0.63
+STIFF_STRONG = 0.45  # dt <= 0.45 tau: up to |v| ~ 0.9 (strong shocks of the batched workload)
+
+
+def cfl_dt(dx: float, tau: float, cfl: float = 0.5, stiff: float = STIFF_SOD) -> float:
+    """Time step rule of the workloads: min(cfl dx, stiff tau). With WENO5 advection at CFL 0.5 the SSP-RK3
+    step is stable for collision stiffness dt gamma (1 + |v|) / tau <= 1.977, hence stiff <= 0.989 for |v| <= 0.6."""
     dt = cfl * dx
     if tau is not None and math.isfinite(tau) and tau > 0:
-        dt = min(dt, 1.25 * tau)
+        dt = min(dt, stiff * tau)
     return dt
 
 
 def sod_tube(Nx: int, Qxi: int, tau: float, Qp: int = 3, Np: int = 2, Nv: int = 5, cfl: float = 0.5,
              bc: int = BC_OPEN, x_left: float = -0.5, length: float = 1.0, left=SOD_LEFT,
-             right=SOD_RIGHT) -> TubeSpec:
+             right=SOD_RIGHT, stiff: float = STIFF_SOD) -> TubeSpec:
     dx = length / Nx
-    return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau, cfl), dx=dx, Qp=Qp, Np=Np, Nv=Nv, bc=bc,
+    return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau, cfl, stiff), dx=dx, Qp=Qp, Np=Np, Nv=Nv, bc=bc,
                     x_left=x_left, left=tuple(left), right=tuple(right))
 
 
@@ -93,7 +100,7 @@ def batched_tubes(ntubes: int = 256, seed: int = BATCH_SEED) -> List[TubeSpec]:
         Qxi = int(rng.choice([8, 16, 32, 64]))
         PL = float(rng.uniform(0.5, 2.0))
         PR = PL * float(rng.uniform(0.01, 0.5))
-        out.append(sod_tube(Nx, Qxi, tau, left=(PL, PL, 0.0), right=(PR, PR / 0.8, 0.0)))
+        out.append(sod_tube(Nx, Qxi, tau, left=(PL, PL, 0.0), right=(PR, PR / 0.8, 0.0), stiff=STIFF_STRONG))
     return out
 
 

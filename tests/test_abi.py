@@ -39,8 +39,8 @@ def test_binding_names_match_header():
 
 def test_suggest_dt_and_error_strings():
     assert rlb.rlb_suggest_dt(1e-4, 1e-4, 0.5) == pytest.approx(5e-5)   # the paper's dt at L_z = 10000
-    assert rlb.rlb_suggest_dt(1 / 400, 1e-3, 0.5) == pytest.approx(1.25e-3)
-    assert rlb.rlb_suggest_dt(1 / 1024, 1e-4, 0.5) == pytest.approx(1.25e-4)
+    assert rlb.rlb_suggest_dt(1 / 400, 1e-3, 0.5) == pytest.approx(0.9e-3)
+    assert rlb.rlb_suggest_dt(1 / 1024, 1e-4, 0.5) == pytest.approx(0.9e-4)
     assert rlb.rlb_suggest_dt(0.01, math.inf, 0.5) == pytest.approx(5e-3)
     for st in range(5):
         assert rlb.rlb_error_string(st).startswith("RLB_")

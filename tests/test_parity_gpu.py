@@ -47,7 +47,7 @@ def test_sod_small_early_steps(nsteps):
 def test_sod_small_full_run_to_t04():
     s = W.sod_small()[0]
     nsteps = int(round(0.4 / s.dt))
-    assert nsteps == 320
+    assert nsteps == 444
     check([s], nsteps)
 
 

@@ -53,11 +53,11 @@ def check_bounds(err, storage):
 @pytest.mark.parametrize("storage", [rb.STORAGE_F32, rb.STORAGE_BF16])
 def test_sod_small_full_run_against_oracle(storage):
     s = W.sod_small()[0]
-    nsteps = 320
+    nsteps = int(round(0.4 / s.dt))  # to t = 0.4
     (f,), _ = run([s], nsteps, storage)
     _, fr = H.oracle_run(s, nsteps)
     err = errors(f, fr)
-    print(f"storage {storage}: Sod Nx=400 Q=24 t=0.4 errors vs FP64 oracle {err}")
+    print(f"storage {storage}: Sod Nx=400 Q=24 t=0.4 ({nsteps} steps) errors vs FP64 oracle {err}")
     check_bounds(err, storage)
 
 
