@@ -265,11 +265,35 @@ def ncu_traffic_per_launch(precision: str, workload: str):
 
 
 # ---------------------------------------------------------------------------------------------------------
+# ranks (torchrun): every rank advances its own replica of the workload; no collective on the data path
+# ---------------------------------------------------------------------------------------------------------
+
+def reduce_max_over_ranks(values, world: int, device: str = "cuda"):
+    """Element-wise max of per-rank timings (the slowest rank sets the job time)."""
+    if world <= 1:
+        return list(values)
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(nodes_per_rank: int, steps: int, world: int, max_seconds: float) -> float:
+    """G velocity-node updates/s of the whole job: the units all ranks processed over the slowest rank's time."""
+    return world * nodes_per_rank * steps / max_seconds / 1e9
+
+
+def rank_prints(rank: int) -> bool:
+    return rank == 0
+
+
+# ---------------------------------------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------------------------------------
 
 def run_reference(args, specs, desc, rank):
-    if rank != 0:
+    if not rank_prints(rank):  # under torchrun only rank 0 runs the CPU reference
         return
     specs, what = cpu_sample(specs)
     pool = OraclePool(specs, host_cores())
@@ -328,11 +352,7 @@ def run_ours(args, specs, desc, rank, world):
     clk = clocks.stop()
     barrier()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_over_ranks([sum(step_ms)], world)[0]
     rb.rlb_sync(h)  # raises if any cell went non-physical during the timed steps
 
     # end to end through the public API with host buffers: H2D of the state from pinned memory, one step,
@@ -348,14 +368,10 @@ def run_ours(args, specs, desc, rank, world):
         rb.rlb_set_state(h, host_state)
         rb.rlb_step(h, 1)
         rb.rlb_moments(h, host_fields)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max_over_ranks([time.perf_counter() - t0], world)[0]
     rb.rlb_destroy(h)
 
-    value = world * nodes * args.steps / (total_ms * 1e-3) / 1e9
+    value = whole_job_rate(nodes, args.steps, world, total_ms * 1e-3)
     stage_ms = total_ms / (3 * args.steps)
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
@@ -395,15 +411,15 @@ def run_ours(args, specs, desc, rank, world):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         "hbm": hbm,
-        "e2e": {"value": world * nodes * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * h.state_size, "d2h_bytes_per_step": 8 * rb.NFIELDS * h.nx_total,
                 "steps": e2e_steps, "api": "rlb_set_state(host) + rlb_step(1) + rlb_moments(host)"},
         "clocks": clk,
         "gpu_launches": 3 * args.steps,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank_prints(rank) and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(specs, desc)
-    if rank == 0:
+    if rank_prints(rank):
         print(json.dumps(line), flush=True)
 
 
