@@ -80,6 +80,8 @@ def _load():
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, ctypes.c_long]
             lib.orc_weno5.argtypes = [ctypes.c_double] * 5
             lib.orc_weno5.restype = ctypes.c_double
+            lib.orc_weno5_population.argtypes = [ctypes.c_double] * 6
+            lib.orc_weno5_population.restype = ctypes.c_double
             lib.orc_rhs.argtypes = [pp, dp, dp]
             lib.orc_step.argtypes = [pp, dp, ctypes.c_long]
             lib.orc_init.argtypes = [pp, dp, dp, dp, dp]
@@ -148,7 +150,13 @@ def feq_cell(Qp: int, Qxi: int, Np: int, Nv: int, n: float, T: float, beta: floa
 
 
 def weno5(vm2, vm1, v0, vp1, vp2) -> float:
+    """Jiang-Shu WENO5 interface value (eps = 1e-6), samples in wind order."""
     return _load().orc_weno5(vm2, vm1, v0, vp1, vp2)
+
+
+def weno5_population(ws, vm2, vm1, v0, vp1, vp2) -> float:
+    """WENO5 of a population whose quadrature weight factor is ws (the scheme on F / ws, scaled back)."""
+    return _load().orc_weno5_population(ws, vm2, vm1, v0, vp1, vp2)
 
 
 def params(Qp=3, Qxi=8, Np=2, Nv=5, Nx=400, dx=None, dt=None, tau=1e-3, bc=BC_OPEN) -> Params:

@@ -25,7 +25,9 @@
  *    orthogonal projection of exp(pbar) f^eq onto L^(1)_l(pbar) P_k(xi), l <= Np, k <= Nv, which is what
  *    makes the moments of Eq. (mom_feq) exact.
  *  - n in f^eq is the Landau density n = -u_mu N^mu (it makes the collision conserve N^mu).
- *  - WENO variant: Jiang-Shu WENO5, eps = 1e-6, applied to F itself, upwind by the sign of xi.
+ *  - WENO variant: Jiang-Shu WENO5, upwind by the sign of xi, applied to the weight-normalised population
+ *    g_s = F_s / (w^p_i w^xi_j / 2) with eps = 1e-6 (equivalently to F_s with eps scaled by the squared
+ *    weight), so that the limiter acts alike on every direction whatever the quadrature order.
  *  - Time integration: Shu-Osher SSP-RK3; the collision uses each stage's own moments.
  *  - Open boundary: three zero-gradient ghost cells per side, refreshed every stage.
  */
@@ -302,7 +304,7 @@ int orc_feq_cell(int Qp, int Qxi, int Np, int Nv, const double *pbar, const doub
  * blowing from v_{-2} toward v_{+2}): three third-order candidates, smoothness indicators with weights 13/12
  * and 1/4, linear weights 1/10, 6/10, 3/10 and alpha_k = d_k / (eps + beta_k)^2.
  */
-double orc_weno5(double vm2, double vm1, double v0, double vp1, double vp2) {
+static double weno5_eps(double eps, double vm2, double vm1, double v0, double vp1, double vp2) {
   double q0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
   double q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
   double q2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
@@ -311,10 +313,21 @@ double orc_weno5(double vm2, double vm1, double v0, double vp1, double vp2) {
   double b1 = 13.0 / 12.0 * (vm1 - 2.0 * v0 + vp1) * (vm1 - 2.0 * v0 + vp1) + 0.25 * (vm1 - vp1) * (vm1 - vp1);
   double b2 = 13.0 / 12.0 * (v0 - 2.0 * vp1 + vp2) * (v0 - 2.0 * vp1 + vp2) +
               0.25 * (3.0 * v0 - 4.0 * vp1 + vp2) * (3.0 * v0 - 4.0 * vp1 + vp2);
-  double a0 = 0.1 / ((WENO_EPS + b0) * (WENO_EPS + b0));
-  double a1 = 0.6 / ((WENO_EPS + b1) * (WENO_EPS + b1));
-  double a2 = 0.3 / ((WENO_EPS + b2) * (WENO_EPS + b2));
+  double a0 = 0.1 / ((eps + b0) * (eps + b0));
+  double a1 = 0.6 / ((eps + b1) * (eps + b1));
+  double a2 = 0.3 / ((eps + b2) * (eps + b2));
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+/* The textbook scheme on O(1) data: eps = 1e-6. */
+double orc_weno5(double vm2, double vm1, double v0, double vp1, double vp2) {
+  return weno5_eps(WENO_EPS, vm2, vm1, v0, vp1, vp2);
+}
+
+/* WENO5 on the population F_s of radial node i, direction j: the scheme applied to g_s = F_s / ws,
+ * ws = w^p_i w^xi_j / 2, then scaled back, which is the scheme on F_s with eps ws^2. */
+double orc_weno5_population(double ws, double vm2, double vm1, double v0, double vp1, double vp2) {
+  return weno5_eps(WENO_EPS * ws * ws, vm2, vm1, v0, vp1, vp2);
 }
 
 /* ------------------------------------------------------------------------------------------------ */
@@ -395,14 +408,15 @@ static int rhs(orc_work *w, const double *G, double *L) {
       int s = i * p->Qxi + j;
       const double *e = w->ext + (size_t)s * Lx; /* e[x + 3] = G[s][x] */
       double xi = w->xi[j];
+      double ws = 0.5 * w->wp[i] * w->wxi[j];
       /* flux[x+1] is the reconstruction at the interface x + 1/2, x = -1 .. Nx-1 */
       for (int x = -1; x < Nx; ++x) {
         const double *c = e + x + 3;
         double phi;
         if (xi > 0.0)
-          phi = orc_weno5(c[-2], c[-1], c[0], c[1], c[2]);
+          phi = orc_weno5_population(ws, c[-2], c[-1], c[0], c[1], c[2]);
         else if (xi < 0.0)
-          phi = orc_weno5(c[3], c[2], c[1], c[0], c[-1]);
+          phi = orc_weno5_population(ws, c[3], c[2], c[1], c[0], c[-1]);
         else
           phi = 0.0;
         w->flux[x + 1] = phi;

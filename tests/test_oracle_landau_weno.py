@@ -106,3 +106,13 @@ def test_weno_mirror_symmetry():
         c = oracle.weno5(*(-v))
         assert c == pytest.approx(-a, rel=1e-14, abs=1e-14)
         assert np.isfinite(b)
+
+
+def test_population_weno_is_the_scheme_on_normalised_values():
+    """The population form applies the eps = 1e-6 scheme to F / ws and scales the result back."""
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        ws = 10.0 ** rng.uniform(-6, 0)
+        g = rng.normal(size=5) * 10.0 ** rng.uniform(-3, 1)
+        got = oracle.weno5_population(ws, *(ws * g))
+        assert got == pytest.approx(ws * oracle.weno5(*g), rel=1e-12, abs=1e-300)

@@ -197,3 +197,16 @@ def test_paper_initial_states():
     f = oracle.fields(p, F)
     np.testing.assert_allclose(f[7], [1.0, 1.0, 0.125, 0.125], rtol=1e-14)
     np.testing.assert_allclose(f[5], [3.0, 3.0, 0.3, 0.3], rtol=1e-14)
+
+
+def test_strong_shock_with_many_directions_stays_physical():
+    """A 60:1 density jump with Qxi = 64 (weak collisions): WENO5 limited on the weight-normalised populations
+    keeps every cell physical; with eps fixed on the weighted populations the small-weight directions fall back
+    to the linear scheme and its undershoot drives the low-density moments negative at the first step."""
+    Nx, Qxi, tau = 64, 64, 1.72e-2
+    dx = 1.0 / 10000
+    p = oracle.params(Qxi=Qxi, Nx=Nx, dx=dx, dt=0.5 * dx, tau=tau)
+    F = oracle.init_riemann(p, left=(1.53, 1.53, 0.0), right=(0.0245, 0.0306, 0.0), xleft=-32 * dx)
+    G = oracle.step(p, F, 30)
+    f = oracle.fields(p, G)
+    assert np.all(f[5] > 0) and np.all(f[7] > 0) and np.all(np.abs(f[6]) < 1)
