@@ -66,6 +66,10 @@ def workload(name: str, nx: int | None = None):
     if name == "stress":
         n = nx or (1 << 20)
         return [W.stress(Nx=n)], f"Sod tube: Nx={n}, Qp=3, Qxi=128, tau=1e-2, CFL 0.5, open BC"
+    if name == "batched":
+        return W.batched_tubes(), ("256 shock tubes, seed 160803004: Nx ~ U[1024,16384], log10 tau ~ U[-4,1], "
+                                   "Qxi in {8,16,32,64}, Qp=3, P_L ~ U[0.5,2], P_R = P_L U(0.01,0.5), "
+                                   "dt=min(0.5dx,0.45tau), open BC")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -335,6 +339,10 @@ def run_ours(args, specs, desc, rank, world):
             torch.distributed.barrier()
 
     h = rb.rlb_init_riemann(tubes, states, xl, stream=stream.cuda_stream)
+    launch = None
+    if args.autotune:
+        best, _ = rb.rlb_autotune(h, 3)
+        launch = best.as_dict()
     for _ in range(args.warmup):
         rb.rlb_step(h, 1)
     rb.rlb_sync(h)
@@ -344,15 +352,21 @@ def run_ours(args, specs, desc, rank, world):
     clocks = ClockSampler(int(visible[dev]) if dev < len(visible) and visible[dev].isdigit() else dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     torch.cuda.synchronize()
+    graph = launch is not None and launch["graph_steps"] > 0
     ev[0].record(stream)
-    for k in range(args.steps):
-        rb.rlb_step(h, 1)
-        ev[k + 1].record(stream)
+    if graph:  # the tuned shape replays captured graphs: time the whole run as one
+        rb.rlb_step(h, args.steps)
+        ev[args.steps].record(stream)
+    else:
+        for k in range(args.steps):
+            rb.rlb_step(h, 1)
+            ev[k + 1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = reduce_max_over_ranks([sum(step_ms)], world)[0]
+    run_ms = ev[0].elapsed_time(ev[args.steps]) if graph else sum(
+        ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
+    total_ms = reduce_max_over_ranks([run_ms], world)[0]
     rb.rlb_sync(h)  # raises if any cell went non-physical during the timed steps
 
     # end to end through the public API with host buffers: H2D of the state from pinned memory, one step,
@@ -405,7 +419,7 @@ def run_ours(args, specs, desc, rank, world):
                                                               args.precision],
         "data": "synthetic",
         "config": {"workload": desc, "velocity_nodes_per_step": nodes, "tubes": len(specs),
-                   "precision": args.precision,
+                   "precision": args.precision, "launch": launch or "one CTA per tile, plain launches",
                    "l2": "inputs larger than L2: state %d B x nodes = %.0f MB per buffer, 3 buffers; no flush"
                          % (esize, esize * nodes / 1e6),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -429,13 +443,20 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "small", "stress"], default="sweep")
-    ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default="f64")
+    ap.add_argument("--workload", choices=["sweep", "small", "stress", "batched"], default="sweep")
+    ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default=None,
+                    help="default f64; f32 for the batched workload (FP32 storage, FP64 moments)")
+    ap.add_argument("--autotune", action="store_true", help="pick the launch shape with rlb_autotune first "
+                    "(default for the batched workload)")
     ap.add_argument("--nx", type=int, default=None, help="cells of the stress tube (default 1048576)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.precision is None:
+        args.precision = "f32" if args.workload == "batched" else "f64"
+    if args.workload == "batched":
+        args.autotune = True
     specs, desc = workload(args.workload, args.nx)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -150,6 +150,40 @@ double rlb_suggest_dt(double dx, double tau, double cfl);
 rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double *pbar, double *wp, double *xi, double *wxi);
 
 /*
+ * Launch shape of a handle's steps (no counterpart in the paper; it changes how the work is scheduled, never
+ * the arithmetic: every choice gives bit-identical results).
+ *   schedule:     RLB_SCHED_TILE (one CTA per tile, the default), RLB_SCHED_STRIDE (persistent grid, tiles by
+ *                 grid stride) or RLB_SCHED_COUNTER (persistent grid, tiles handed out by an atomic counter;
+ *                 no CTA waits on another).
+ *   ctas_per_sm:  persistent grid = SMs x ctas_per_sm; 0 takes the occupancy limit.
+ *   graph_steps:  rlb_step replays a captured CUDA graph of this many steps (on a private stream joined to the
+ *                 handle's stream by events); 0 launches directly. Calls made while the handle's stream is
+ *                 being captured by the caller always launch directly. 1 <= graph_steps <= 64 otherwise.
+ *   order:        tile order, RLB_ORDER_COST (most expensive tubes first, the default) or RLB_ORDER_INTERLEAVE
+ *                 (tubes interleaved tile by tile).
+ */
+enum { RLB_SCHED_TILE = 0, RLB_SCHED_STRIDE = 1, RLB_SCHED_COUNTER = 2 };
+enum { RLB_ORDER_COST = 0, RLB_ORDER_INTERLEAVE = 1 };
+typedef struct {
+  int32_t schedule;
+  int32_t ctas_per_sm;
+  int32_t graph_steps;
+  int32_t order;
+} rlb_launch;
+
+/* rlb_get_launch / rlb_set_launch - read or change the launch shape (RLB_EINVAL for values out of range). */
+rlb_status rlb_get_launch(rlb_handle h, rlb_launch *out);
+rlb_status rlb_set_launch(rlb_handle h, const rlb_launch *cfg);
+
+/*
+ * rlb_autotune - time every launch shape (schedules x ctas_per_sm in {occupancy, 1, 2} x both tile orders x
+ *   graph on/off) for trial_steps steps on the handle's own tubes and state, keep the fastest. The state is
+ *   saved first and restored after every trial, so the handle's state is unchanged on return. best and
+ *   best_ms_per_step (either may be NULL) receive the choice and its time per step. Synchronous.
+ */
+rlb_status rlb_autotune(rlb_handle h, int32_t trial_steps, rlb_launch *best, double *best_ms_per_step);
+
+/*
  * rlb_step_static - advance ONE tube by nsteps SSP-RK3 steps without allocating device memory.
  *   This entry point has no counterpart in the paper; it exists for callers that cannot call cudaMalloc
  *   (or anything that allocates device memory) at the point where they step: a host application that has

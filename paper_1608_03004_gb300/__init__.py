@@ -16,17 +16,26 @@ from .binding import (  # noqa: F401
     STORAGE_F32,
     STORAGE_F64,
     Handle,
+    Launch,
+    ORDER_COST,
+    ORDER_INTERLEAVE,
+    SCHED_COUNTER,
+    SCHED_STRIDE,
+    SCHED_TILE,
     RlbError,
     Tube,
     library_path,
     load,
     rlb_destroy,
+    rlb_autotune,
     rlb_error_string,
+    rlb_get_launch,
     rlb_get_state,
     rlb_init,
     rlb_init_riemann,
     rlb_moments,
     rlb_quadrature,
+    rlb_set_launch,
     rlb_set_state,
     rlb_state_size,
     rlb_step,

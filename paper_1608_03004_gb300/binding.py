@@ -59,6 +59,20 @@ class Tube(ctypes.Structure):
         return cls(Qp, Qxi, Np, Nv, Nx, dx, dt, tau_c, bc, storage)
 
 
+SCHED_TILE, SCHED_STRIDE, SCHED_COUNTER = 0, 1, 2
+ORDER_COST, ORDER_INTERLEAVE = 0, 1
+
+
+class Launch(ctypes.Structure):
+    """rlb_launch: scheduling of a handle's steps (never changes results)."""
+
+    _fields_ = [("schedule", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+                ("order", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -95,6 +109,9 @@ def load():
             "rlb_suggest_dt": ([ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_double),
             "rlb_quadrature": ([ip, ip, dp, dp, dp, dp], ctypes.c_int),
             "rlb_step_static": ([tp, vp, vp, ctypes.c_int64, vp, vp], ctypes.c_int),
+            "rlb_get_launch": ([vp, ctypes.POINTER(Launch)], ctypes.c_int),
+            "rlb_set_launch": ([vp, ctypes.POINTER(Launch)], ctypes.c_int),
+            "rlb_autotune": ([vp, ip, ctypes.POINTER(Launch), dp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -301,3 +318,23 @@ def rlb_step_static(tube: Tube, F_in, F_out, nsteps: int, flag=None, stream=None
         fp = ctypes.c_void_p(flag.data_ptr())
     _check(load().rlb_step_static(ctypes.byref(tube), _dev_ptr(F_in, n), _dev_ptr(F_out, n), int(nsteps), fp,
                                   _stream(stream)), "rlb_step_static")
+
+
+def rlb_get_launch(h: Handle) -> Launch:
+    out = Launch()
+    _check(load().rlb_get_launch(h.ptr, ctypes.byref(out)), "rlb_get_launch")
+    return out
+
+
+def rlb_set_launch(h: Handle, cfg: Launch | dict) -> None:
+    if isinstance(cfg, dict):
+        cfg = Launch(**cfg)
+    _check(load().rlb_set_launch(h.ptr, ctypes.byref(cfg)), "rlb_set_launch")
+
+
+def rlb_autotune(h: Handle, trial_steps: int = 3):
+    """Time every launch shape on this handle's tubes and keep the fastest; returns (Launch, ms per step)."""
+    best = Launch()
+    ms = ctypes.c_double()
+    _check(load().rlb_autotune(h.ptr, int(trial_steps), ctypes.byref(best), ctypes.byref(ms)), "rlb_autotune")
+    return best, ms.value

@@ -60,7 +60,37 @@ struct StageArgs {
   int* flag;
   double a, b;        // Shu-Osher combination F_out = a F^n + b (F_in + dt L(F_in))
   int stage;          // 0, 1, 2: selects the b dt xi / dx table
+  int ntiles;         // tiles of this launch
+  int schedule;       // 0: one CTA per tile; 1: persistent, grid stride; 2: persistent, work counter
+  int* counter;       // work counter of schedule 2 (zeroed before the launch)
 };
+
+// Tile loop of a stage launch. Schedule 0 gives each CTA one tile; the persistent schedules keep a grid of
+// about one wave resident and hand out tiles by a grid stride or by an atomic work counter (cost-ordered
+// tiles then balance uneven tubes). No CTA ever waits on another.
+template <typename Body>
+__device__ __forceinline__ void for_each_tile(int ntiles, int schedule, int* counter, Body body) {
+  if (schedule == 0) {
+    body((int)blockIdx.x);
+    return;
+  }
+  if (schedule == 1) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      __syncthreads();  // the previous tile's shared-memory readers are done
+      body(t);
+    }
+    return;
+  }
+  __shared__ int next_tile;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) next_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = next_tile;
+    if (t >= ntiles) return;
+    body(t);
+  }
+}
 
 // --------------------------------------------------------------------------------------------------
 // Device helpers
@@ -303,8 +333,9 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
     if (rv) {
       const int p = c + (fwd ? 1 : 2);
       const double x = row[p] - row[p - 1], y = row[p + 1] - row[p];
+      const double* et = tab + tab_eps(Qxi) + 3 * s;
       double sa, sb, sc;
-      weno5_pair(x, y, fwd, sa, sb, sc);
+      weno5_pair(x, y, fwd, et[0], et[1], et[2], sa, sb, sc);
       sp0[c] = sa;
       sp1[c] = sb;
       sp2[c] = sc;
@@ -347,15 +378,19 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
   }
 }
 
+// SCHED is the launch's schedule (compile time, so that the one-CTA-per-tile kernel carries no tile loop).
+template <int SCHED>
 __global__ void __launch_bounds__(NT, 4) rlb_stage_kernel(StageArgs A) {
   extern __shared__ __align__(16) unsigned char stage_smem_raw[];
   StageSmem& sm = *reinterpret_cast<StageSmem*>(stage_smem_raw);
-  const int2 tl = A.tiles[blockIdx.x];
-  const TubeDev T = A.tubes[tl.x];
-  if (T.Np == 2 && T.Nv == 5)
-    stage_tile<2, 5>(A, T, tl.y, sm);
-  else
-    stage_tile<NP_MAX, NV_MAX>(A, T, tl.y, sm);
+  for_each_tile(A.ntiles, SCHED, A.counter, [&](int t) {
+    const int2 tl = A.tiles[t];
+    const TubeDev T = A.tubes[tl.x];
+    if (T.Np == 2 && T.Nv == 5)
+      stage_tile<2, 5>(A, T, tl.y, sm);
+    else
+      stage_tile<NP_MAX, NV_MAX>(A, T, tl.y, sm);
+  });
 }
 
 #include "rlb_stage_rp.cuh"
@@ -576,12 +611,16 @@ rlb_status ensure_series_tables(int dev) {
   }
   RLB_CUDA(cudaMemcpyToSymbol(g_ic, ic.data(), ic.size() * sizeof(double)));
   RLB_CUDA(cudaMemcpyToSymbol(g_cb, cb.data(), cb.size() * sizeof(double)));
-  RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(StageSmem)));
-  RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_stage_rp_kernel<float>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmemRP)));
-  RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_stage_rp_kernel<__nv_bfloat16>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmemRP)));
+  const void* fp64[3] = {(const void*)rlb_stage_kernel<0>, (const void*)rlb_stage_kernel<1>,
+                         (const void*)rlb_stage_kernel<2>};
+  const void* rp[6] = {(const void*)rlb_stage_rp_kernel<float, 0>, (const void*)rlb_stage_rp_kernel<float, 1>,
+                       (const void*)rlb_stage_rp_kernel<float, 2>, (const void*)rlb_stage_rp_kernel<__nv_bfloat16, 0>,
+                       (const void*)rlb_stage_rp_kernel<__nv_bfloat16, 1>,
+                       (const void*)rlb_stage_rp_kernel<__nv_bfloat16, 2>};
+  for (const void* k : fp64)
+    RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmem)));
+  for (const void* k : rp)
+    RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmemRP)));
   g_tables_ready[dev] = true;
   return RLB_OK;
 }
@@ -610,13 +649,28 @@ struct rlb_ctx {
                                                        // ([RLB_NFIELDS][nxtot]; the first 5 rows are used)
   int* d_flag = nullptr;
   int* h_flag = nullptr;       // pinned
+  // launch shape, CUDA graph of graph_steps steps, work counters of the counter schedule
+  rlb_launch cfg = {RLB_SCHED_TILE, 0, 0, RLB_ORDER_COST};
+  int occupancy = 1;           // resident CTAs per SM of the stage kernel
+  int nsm = 1;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int* d_counters = nullptr;   // 3 per step, GRAPH_MAX steps
 };
 
 namespace {
 
+constexpr int GRAPH_MAX = 64;  // longest captured graph, in steps
+
 void free_ctx(rlb_ctx* h) {
   if (!h) return;
   DeviceGuard gd(h->dev);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
+  cudaFree(h->d_counters);
   cudaFree(h->d_tubes);
   cudaFree(h->d_tiles);
   cudaFree(h->d_tab);
@@ -632,6 +686,47 @@ void free_ctx(rlb_ctx* h) {
   cudaFree(h->d_flag);
   cudaFreeHost(h->h_flag);
   delete h;
+}
+
+// WENO5 epsilon terms of every velocity: 3 eps ws^2 (C0, C1, C2), ws = w^p_i w^xi_j / 2 (the limiter acts on
+// the weight-normalised population F_s / ws with eps = 1e-6).
+void fill_eps(double* out, int Qp, int Qxi, const double* wp, const double* wxi) {
+  for (int i = 0; i < Qp; ++i)
+    for (int j = 0; j < Qxi; ++j) {
+      const double ws = 0.5 * wp[i] * wxi[j];
+      const double e = 3.0 * rlbdev::WENO_EPS * ws * ws;
+      double* o = out + 3 * (i * Qxi + j);
+      o[0] = e * rlbdev::C0;
+      o[1] = e * rlbdev::C1;
+      o[2] = e * rlbdev::C2;
+    }
+}
+
+// Tiles of TX cells of every tube: most expensive tubes first (RLB_ORDER_COST), or those tubes interleaved
+// tile by tile (RLB_ORDER_INTERLEAVE).
+std::vector<int2> build_tiles(const std::vector<rlb_tube>& tubes, int order) {
+  const int ntubes = (int)tubes.size();
+  std::vector<int> ord(ntubes);
+  for (int b = 0; b < ntubes; ++b) ord[b] = b;
+  std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) {
+    return tubes[p].Qp * tubes[p].Qxi > tubes[q].Qp * tubes[q].Qxi;
+  });
+  std::vector<int2> tiles;
+  if (order == RLB_ORDER_COST) {
+    for (int b : ord)
+      for (int x0 = 0; x0 < (int)tubes[b].Nx; x0 += TX) tiles.push_back(make_int2(b, x0));
+  } else {
+    bool more = true;
+    for (int x0 = 0; more; x0 += TX) {
+      more = false;
+      for (int b : ord)
+        if (x0 < (int)tubes[b].Nx) {
+          tiles.push_back(make_int2(b, x0));
+          more = true;
+        }
+    }
+  }
+  return tiles;
 }
 
 rlb_status validate(const rlb_tube* t) {
@@ -692,8 +787,8 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     h->packed += (long long)t.Qp * t.Qxi * t.Nx;
     d.tab = (int)tab.size();
     d.tabf = (int)tabf.size();
-    tab.resize(tab.size() + tab_size(t.Qxi), 0.0);
-    tabf.resize(tabf.size() + tabf_size(t.Qxi), 0.0f);
+    tab.resize(tab.size() + tab_size(t.Qp, t.Qxi), 0.0);
+    tabf.resize(tabf.size() + tabf_size(t.Qp, t.Qxi), 0.0f);
     double* T = tab.data() + d.tab;
     std::vector<double> pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
     if (!rlbq::gauss_laguerre1(t.Qp, pb.data(), wp.data()) || !rlbq::gauss_legendre(t.Qxi, xi.data(), wxi.data()))
@@ -719,6 +814,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
         T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
       for (int st = 0; st < 3; ++st) T[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
     }
+    fill_eps(T + tab_eps(t.Qxi), t.Qp, t.Qxi, wp.data(), wxi.data());
     // FP32 tables: hi/lo float pairs of the moment weights, and FP32 copies of the per-row factors
     float* Tf = tabf.data() + d.tabf;
     auto split = [](double w, float& hi, float& lo) {
@@ -735,18 +831,13 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
       for (int k = 0; k <= NV_MAX; ++k) Tf[tabf_pw(t.Qxi) + j * (NV_MAX + 1) + k] = (float)T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k];
       for (int st = 0; st < 3; ++st) Tf[tabf_cxi(t.Qxi) + st * t.Qxi + j] = (float)T[tab_cxi(t.Qxi) + st * t.Qxi + j];
     }
+    for (int i = 0; i < t.Qp; ++i)
+      for (int j = 0; j < t.Qxi; ++j) Tf[tabf_iws(t.Qxi) + i * t.Qxi + j] = (float)(2.0 / (wp[i] * wxi[j]));
   }
   h->state_elems = off;
   h->nxtot = xoff;
   // tiles, most expensive tubes first
-  std::vector<int> order(ntubes);
-  for (int b = 0; b < ntubes; ++b) order[b] = b;
-  std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
-    return tubes[p].Qp * tubes[p].Qxi > tubes[q].Qp * tubes[q].Qxi;
-  });
-  std::vector<int2> tiles;
-  for (int b : order)
-    for (int x0 = 0; x0 < (int)tubes[b].Nx; x0 += TX) tiles.push_back(make_int2(b, x0));
+  const std::vector<int2> tiles = build_tiles(h->tubes, RLB_ORDER_COST);
   h->ntiles = (int)tiles.size();
   DeviceGuard gd(h->dev);
   RLB_CUDA(cudaMalloc(&h->d_tubes, sizeof(TubeDev) * ntubes));
@@ -758,6 +849,11 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaMalloc(&h->F2, h->esize * h->state_elems));
   RLB_CUDA(cudaMalloc(&h->d_flag, sizeof(int)));
   RLB_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
+  RLB_CUDA(cudaMalloc(&h->d_counters, sizeof(int) * 3 * GRAPH_MAX));
+  RLB_CUDA(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+  RLB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  RLB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  RLB_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
   if (h->storage != RLB_STORAGE_F64) {
     RLB_CUDA(cudaMalloc(&h->M, sizeof(double) * RLB_NFIELDS * h->nxtot));
     RLB_CUDA(cudaMalloc(&h->M1, sizeof(double) * RLB_NFIELDS * h->nxtot));
@@ -773,6 +869,16 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
   rlb_status st = ensure_series_tables(h->dev);
   if (st != RLB_OK) return st;
+  // resident CTAs per SM of this handle's stage kernel (the persistent grids' default size)
+  if (h->storage == RLB_STORAGE_F64)
+    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_kernel<1>, NT, sizeof(StageSmem)));
+  else if (h->storage == RLB_STORAGE_F32)
+    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_rp_kernel<float, 1>, NT,
+                                                           sizeof(StageSmemRP)));
+  else
+    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_rp_kernel<__nv_bfloat16, 1>, NT,
+                                                           sizeof(StageSmemRP)));
+  if (h->occupancy < 1) h->occupancy = 1;
   return RLB_OK;
 }
 
@@ -884,40 +990,58 @@ rlb_status rlb_init_riemann(rlb_handle* out, const rlb_tube* tubes, int32_t ntub
   return RLB_OK;
 }
 
-rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
-  if (!h || nsteps < 0) return RLB_EINVAL;
-  DeviceGuard gd(h->dev);
+}  // extern "C"
+
+namespace {
+
+// nsteps steps as plain launches on `stream`. in_graph: the launches belong to one captured graph, whose
+// counter-schedule launches get counters of their own (zeroed once up front), else each step zeroes three.
+rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in_graph) {
   const void* in[3] = {h->F, h->F1, h->F2};
   void* out[3] = {h->F1, h->F2, h->F};
-  if (h->storage == RLB_STORAGE_F64) {
-    StageArgs A{};
-    A.tubes = h->d_tubes;
-    A.tiles = h->d_tiles;
-    A.tab = h->d_tab;
-    A.flag = h->d_flag;
-    A.Fn = static_cast<const double*>(h->F);
-    for (int64_t t = 0; t < nsteps; ++t)
-      for (int st = 0; st < 3; ++st) {
+  const int sched = h->cfg.schedule;
+  const int grid = sched == RLB_SCHED_TILE
+                       ? h->ntiles
+                       : std::max(1, std::min(h->ntiles, h->nsm * (h->cfg.ctas_per_sm > 0 ? h->cfg.ctas_per_sm
+                                                                                          : h->occupancy)));
+  if (sched == RLB_SCHED_COUNTER && in_graph)
+    RLB_CUDA(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 3 * nsteps, stream));
+  for (int64_t t = 0; t < nsteps; ++t) {
+    if (sched == RLB_SCHED_COUNTER && !in_graph) RLB_CUDA(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 3, stream));
+    int* ctr = h->d_counters + (in_graph ? 3 * t : 0);
+    for (int st = 0; st < 3; ++st) {
+      if (h->storage == RLB_STORAGE_F64) {
+        StageArgs A{};
+        A.tubes = h->d_tubes;
+        A.tiles = h->d_tiles;
+        A.tab = h->d_tab;
+        A.flag = h->d_flag;
+        A.Fn = static_cast<const double*>(h->F);
         A.Fin = static_cast<const double*>(in[st]);
         A.Fout = static_cast<double*>(out[st]);
         A.a = RK_A[st];
         A.b = RK_B[st];
         A.stage = st;
-        rlb_stage_kernel<<<h->ntiles, NT, sizeof(StageSmem), h->stream>>>(A);
-      }
-  } else {
-    StageArgsRP A{};
-    A.tubes = h->d_tubes;
-    A.tiles = h->d_tiles;
-    A.tab = h->d_tab;
-    A.tabf = h->d_tabf;
-    A.flag = h->d_flag;
-    A.Fn = h->F;
-    A.nxtot = h->nxtot;
-    const double* min[3] = {h->M, h->M1, h->M2};
-    double* mout[3] = {h->M1, h->M2, h->M};
-    for (int64_t t = 0; t < nsteps; ++t)
-      for (int st = 0; st < 3; ++st) {
+        A.ntiles = h->ntiles;
+        A.schedule = sched;
+        A.counter = ctr + st;
+        if (sched == RLB_SCHED_TILE)
+          rlb_stage_kernel<0><<<grid, NT, sizeof(StageSmem), stream>>>(A);
+        else if (sched == RLB_SCHED_STRIDE)
+          rlb_stage_kernel<1><<<grid, NT, sizeof(StageSmem), stream>>>(A);
+        else
+          rlb_stage_kernel<2><<<grid, NT, sizeof(StageSmem), stream>>>(A);
+      } else {
+        const double* min[3] = {h->M, h->M1, h->M2};
+        double* mout[3] = {h->M1, h->M2, h->M};
+        StageArgsRP A{};
+        A.tubes = h->d_tubes;
+        A.tiles = h->d_tiles;
+        A.tab = h->d_tab;
+        A.tabf = h->d_tabf;
+        A.flag = h->d_flag;
+        A.Fn = h->F;
+        A.nxtot = h->nxtot;
         A.Fin = in[st];
         A.Fout = out[st];
         A.Min = min[st];
@@ -926,13 +1050,152 @@ rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
         A.b = (float)RK_B[st];
         A.bd = RK_B[st];
         A.stage = st;
-        if (h->storage == RLB_STORAGE_F32)
-          rlb_stage_rp_kernel<float><<<h->ntiles, NT, sizeof(StageSmemRP), h->stream>>>(A);
-        else
-          rlb_stage_rp_kernel<__nv_bfloat16><<<h->ntiles, NT, sizeof(StageSmemRP), h->stream>>>(A);
+        A.ntiles = h->ntiles;
+        A.schedule = sched;
+        A.counter = ctr + st;
+        const size_t sb = sizeof(StageSmemRP);
+        if (h->storage == RLB_STORAGE_F32) {
+          if (sched == RLB_SCHED_TILE)
+            rlb_stage_rp_kernel<float, 0><<<grid, NT, sb, stream>>>(A);
+          else if (sched == RLB_SCHED_STRIDE)
+            rlb_stage_rp_kernel<float, 1><<<grid, NT, sb, stream>>>(A);
+          else
+            rlb_stage_rp_kernel<float, 2><<<grid, NT, sb, stream>>>(A);
+        } else {
+          if (sched == RLB_SCHED_TILE)
+            rlb_stage_rp_kernel<__nv_bfloat16, 0><<<grid, NT, sb, stream>>>(A);
+          else if (sched == RLB_SCHED_STRIDE)
+            rlb_stage_rp_kernel<__nv_bfloat16, 1><<<grid, NT, sb, stream>>>(A);
+          else
+            rlb_stage_rp_kernel<__nv_bfloat16, 2><<<grid, NT, sb, stream>>>(A);
+        }
       }
+    }
   }
   return cuda_status(cudaGetLastError());
+}
+
+// Capture graph_steps steps on the private stream (once per launch shape).
+rlb_status ensure_graph(rlb_ctx* h) {
+  if (h->gexec) return RLB_OK;
+  cudaGraph_t graph = nullptr;
+  RLB_CUDA(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
+  const rlb_status st = launch_steps(h, h->gstream, h->cfg.graph_steps, true);
+  const cudaError_t e = cudaStreamEndCapture(h->gstream, &graph);
+  if (st != RLB_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  RLB_CUDA(e);
+  const cudaError_t ei = cudaGraphInstantiate(&h->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  return cuda_status(ei);
+}
+
+void drop_graph(rlb_ctx* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
+  if (!h || nsteps < 0) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  const int G = h->cfg.graph_steps;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RLB_CUDA(cudaStreamIsCapturing(h->stream, &cap));
+  if (G <= 0 || nsteps < G || cap != cudaStreamCaptureStatusNone) return launch_steps(h, h->stream, nsteps, false);
+  rlb_status st = ensure_graph(h);
+  if (st != RLB_OK) return st;
+  RLB_CUDA(cudaEventRecord(h->ev_fork, h->stream));
+  RLB_CUDA(cudaStreamWaitEvent(h->gstream, h->ev_fork, 0));
+  for (int64_t k = 0; k < nsteps / G; ++k) RLB_CUDA(cudaGraphLaunch(h->gexec, h->gstream));
+  st = launch_steps(h, h->gstream, nsteps % G, false);
+  RLB_CUDA(cudaEventRecord(h->ev_join, h->gstream));
+  RLB_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  return st;
+}
+
+rlb_status rlb_get_launch(rlb_handle h, rlb_launch* out) {
+  if (!h || !out) return RLB_EINVAL;
+  *out = h->cfg;
+  return RLB_OK;
+}
+
+rlb_status rlb_set_launch(rlb_handle h, const rlb_launch* cfg) {
+  if (!h || !cfg) return RLB_EINVAL;
+  if (cfg->schedule < RLB_SCHED_TILE || cfg->schedule > RLB_SCHED_COUNTER || cfg->ctas_per_sm < 0 ||
+      cfg->ctas_per_sm > 64 || cfg->graph_steps < 0 || cfg->graph_steps > GRAPH_MAX ||
+      (cfg->order != RLB_ORDER_COST && cfg->order != RLB_ORDER_INTERLEAVE))
+    return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  if (cfg->order != h->cfg.order) {
+    const std::vector<int2> tiles = build_tiles(h->tubes, cfg->order);
+    RLB_CUDA(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+    RLB_CUDA(cudaStreamSynchronize(h->stream));  // the host vector goes out of scope
+  }
+  drop_graph(h);
+  h->cfg = *cfg;
+  return RLB_OK;
+}
+
+rlb_status rlb_autotune(rlb_handle h, int32_t trial_steps, rlb_launch* best, double* best_ms_per_step) {
+  if (!h || trial_steps < 1 || trial_steps > GRAPH_MAX) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  // save the state (and, for reduced storage, the moments the first stage reads)
+  const size_t fbytes = h->esize * h->state_elems;
+  const size_t mbytes = h->M ? sizeof(double) * RLB_NFIELDS * h->nxtot : 0;
+  char* saved = nullptr;
+  RLB_CUDA(cudaMalloc(&saved, fbytes + mbytes));
+  auto restore = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(h->F, saved, fbytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && mbytes) e = cudaMemcpyAsync(h->M, saved + fbytes, mbytes, cudaMemcpyDeviceToDevice, h->stream);
+    return e;
+  };
+  cudaError_t e = cudaMemcpyAsync(saved, h->F, fbytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess && mbytes) e = cudaMemcpyAsync(saved + fbytes, h->M, mbytes, cudaMemcpyDeviceToDevice, h->stream);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  const rlb_launch start = h->cfg;
+  rlb_launch win = start;
+  float win_ms = -1.0f;
+  rlb_status st = cuda_status(e);
+  const int scheds[7][2] = {{RLB_SCHED_TILE, 0}, {RLB_SCHED_STRIDE, 0}, {RLB_SCHED_STRIDE, 1}, {RLB_SCHED_STRIDE, 2},
+                            {RLB_SCHED_COUNTER, 0}, {RLB_SCHED_COUNTER, 1}, {RLB_SCHED_COUNTER, 2}};
+  for (int order = 0; order < 2 && st == RLB_OK; ++order)
+    for (int k = 0; k < 7 && st == RLB_OK; ++k)
+      for (int graph = 0; graph < 2 && st == RLB_OK; ++graph) {
+        const rlb_launch c = {scheds[k][0], scheds[k][1], graph ? trial_steps : 0, order};
+        st = rlb_set_launch(h, &c);
+        if (st == RLB_OK) st = rlb_step(h, trial_steps);  // warm-up (and graph capture)
+        if (st == RLB_OK) st = cuda_status(restore());
+        if (st == RLB_OK) st = cuda_status(cudaEventRecord(t0, h->stream));
+        if (st == RLB_OK) st = rlb_step(h, trial_steps);
+        if (st == RLB_OK) st = cuda_status(cudaEventRecord(t1, h->stream));
+        if (st == RLB_OK) st = cuda_status(cudaEventSynchronize(t1));
+        float ms = 0.0f;
+        if (st == RLB_OK) st = cuda_status(cudaEventElapsedTime(&ms, t0, t1));
+        if (st == RLB_OK && (win_ms < 0.0f || ms < win_ms)) {
+          win_ms = ms;
+          win = c;
+        }
+        if (st == RLB_OK) st = cuda_status(restore());
+      }
+  if (st == RLB_OK) st = rlb_set_launch(h, &win);
+  else rlb_set_launch(h, &start);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(saved);
+  if (st != RLB_OK) return st;
+  if (best) *best = win;
+  if (best_ms_per_step) *best_ms_per_step = win_ms / trial_steps;
+  return check_flag(h);
 }
 
 rlb_status rlb_moments(rlb_handle h, double* out, int32_t out_on_device) {
@@ -1127,7 +1390,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
   const size_t off_tiles = align256(sizeof(TubeDev));
   const size_t off_flag = off_tiles + align256(sizeof(int2) * (size_t)ntiles);
   const size_t off_tab = off_flag + 256;
-  const size_t off_f1 = off_tab + align256(sizeof(double) * (size_t)tab_size(t.Qxi));
+  const size_t off_f1 = off_tab + align256(sizeof(double) * (size_t)tab_size(t.Qp, t.Qxi));
   const size_t stage_bytes = align256(sizeof(double) * (size_t)Q * (size_t)Nx);
   const size_t off_f2 = off_f1 + stage_bytes;
   if (off_f2 + stage_bytes > (size_t)RLB_STATIC_SCRATCH_BYTES) return RLB_EINVAL;
@@ -1161,7 +1424,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
   d.index = 0;
   std::vector<int2> tiles(ntiles);
   for (int k = 0; k < ntiles; ++k) tiles[k] = make_int2(0, k * TX);
-  std::vector<double> tab(tab_size(t.Qxi), 0.0), pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
+  std::vector<double> tab(tab_size(t.Qp, t.Qxi), 0.0), pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
   if (!rlbq::gauss_laguerre1(t.Qp, pb.data(), wp.data()) || !rlbq::gauss_legendre(t.Qxi, xi.data(), wxi.data()))
     return RLB_EINVAL;
   for (int i = 0; i < t.Qp; ++i) {
@@ -1184,6 +1447,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
       tab[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
     for (int st = 0; st < 3; ++st) tab[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
   }
+  fill_eps(tab.data() + tab_eps(t.Qxi), t.Qp, t.Qxi, wp.data(), wxi.data());
   RLB_CUDA(cudaMemcpyAsync(b, &d, sizeof(TubeDev), cudaMemcpyHostToDevice, s));
   RLB_CUDA(cudaMemcpyAsync(b + off_tiles, tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice, s));
   RLB_CUDA(cudaMemcpyAsync(b + off_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s));
@@ -1209,7 +1473,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
       A.a = RK_A[st];
       A.b = RK_B[st];
       A.stage = st;
-      rlb_stage_kernel<<<ntiles, NT, sizeof(StageSmem), s>>>(A);
+      rlb_stage_kernel<0><<<ntiles, NT, sizeof(StageSmem), s>>>(A);
     }
   }
   return cuda_status(cudaGetLastError());

@@ -32,7 +32,10 @@ constexpr double WENO_EPS = 1e-6;
 constexpr double C0 = 3.1622776601683795;  // sqrt(10)
 constexpr double C1 = 1.2909944487358056;  // sqrt(10/6)
 constexpr double C2 = 1.8257418583505538;  // sqrt(10/3)
-constexpr double E3 = 3.0 * WENO_EPS;
+// epsilon terms 3 eps (C0, C1, C2) of indicators taken on weight-normalised values
+constexpr float EPS_A = (float)(3.0 * WENO_EPS * C0);
+constexpr float EPS_B = (float)(3.0 * WENO_EPS * C1);
+constexpr float EPS_C = (float)(3.0 * WENO_EPS * C2);
 
 // Reciprocal used by the WENO combination: FP64 as above; FP32 the hardware approximation alone (about 1 ulp
 // of FP32, below the rounding of the FP32 state it serves).
@@ -45,15 +48,16 @@ __device__ __forceinline__ float rcp_fast(float d) {
 
 // Scaled indicator squares of the pair (x, y) = (d_j, d_{j+1}) in memory order. fwd: wind toward increasing
 // index; then sA = (C0 (SL + 3eps))^2, sB = (C1 (SC + 3eps))^2, sC = (C2 (SR + 3eps))^2; otherwise SL and SR
-// trade places. T is double (FP64 path) or float (reduced-precision path).
+// trade places. (eA, eB, eC) = 3 eps (C0, C1, C2): the velocity's epsilon term, which scales with the square
+// of its quadrature weight. T is double (FP64 path) or float (reduced-precision path).
 template <typename T>
-__device__ __forceinline__ void weno5_pair(T x, T y, bool fwd, T& sA, T& sB, T& sC) {
+__device__ __forceinline__ void weno5_pair(T x, T y, bool fwd, T eA, T eB, T eC, T& sA, T& sB, T& sC) {
   const T qx = x * x, pxy = x * y, qy = y * y;
   const T ax = fwd ? T(4.0 * C0) : T(10.0 * C0), ay = fwd ? T(10.0 * C0) : T(4.0 * C0);
   const T cx = fwd ? T(10.0 * C2) : T(4.0 * C2), cy = fwd ? T(4.0 * C2) : T(10.0 * C2);
-  const T uA = fma(ax, qx, fma(T(-11.0 * C0), pxy, fma(ay, qy, T(E3 * C0))));
-  const T uB = fma(T(4.0 * C1), qx, fma(T(-5.0 * C1), pxy, fma(T(4.0 * C1), qy, T(E3 * C1))));
-  const T uC = fma(cx, qx, fma(T(-11.0 * C2), pxy, fma(cy, qy, T(E3 * C2))));
+  const T uA = fma(ax, qx, fma(T(-11.0 * C0), pxy, fma(ay, qy, eA)));
+  const T uB = fma(T(4.0 * C1), qx, fma(T(-5.0 * C1), pxy, fma(T(4.0 * C1), qy, eB)));
+  const T uC = fma(cx, qx, fma(T(-11.0 * C2), pxy, fma(cy, qy, eC)));
   sA = uA * uA;
   sB = uB * uB;
   sC = uC * uC;
@@ -72,14 +76,15 @@ __device__ __forceinline__ T weno5_combine(T s0, T s1, T s2, T d1, T d2, T d3, T
 
 // Interface value v2 + G of five samples in memory order m0..m4 around the interface between m2 and m3
 // (wind toward increasing index, fwd) or between m1 and m2 (wind toward decreasing index), computed
-// exactly as the stage kernels do: pairs first, then the combination.
+// exactly as the stage kernels do: pairs first, then the combination. eps: the limiter's epsilon.
 template <typename T>
-__device__ __forceinline__ T weno5_interface(T m0, T m1, T m2, T m3, T m4, bool fwd) {
+__device__ __forceinline__ T weno5_interface(T m0, T m1, T m2, T m3, T m4, bool fwd, double eps = WENO_EPS) {
   const T D1 = m1 - m0, D2 = m2 - m1, D3 = m3 - m2, D4 = m4 - m3;
+  const T eA = T(3.0 * eps * C0), eB = T(3.0 * eps * C1), eC = T(3.0 * eps * C2);
   T a[3], b[3], c[3];
-  weno5_pair(D1, D2, fwd, a[0], b[0], c[0]);
-  weno5_pair(D2, D3, fwd, a[1], b[1], c[1]);
-  weno5_pair(D3, D4, fwd, a[2], b[2], c[2]);
+  weno5_pair(D1, D2, fwd, eA, eB, eC, a[0], b[0], c[0]);
+  weno5_pair(D2, D3, fwd, eA, eB, eC, a[1], b[1], c[1]);
+  weno5_pair(D3, D4, fwd, eA, eB, eC, a[2], b[2], c[2]);
   if (fwd) return m2 + weno5_combine(a[0], b[1], c[2], D1, D2, D3, D4);
   return m2 + weno5_combine(a[2], b[1], c[0], -D4, -D3, -D2, -D1);
 }

@@ -50,7 +50,9 @@ struct TubeDev {
 //                                               at [i (NP_MAX+1) + q]: the radial factor multiplying
 //                                               s^(q+2) hhat_{q+2,k} in the truncated equilibrium
 //   then xi_j (Qxi), then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k] (Qxi (NV_MAX+1)), zero for k > Nv,
-//   then b_st dt xi_j / dx at [st Qxi + j] for the three Runge-Kutta stages, b = (1, 1/4, 2/3)
+//   then b_st dt xi_j / dx at [st Qxi + j] for the three Runge-Kutta stages, b = (1, 1/4, 2/3),
+//   then per velocity s = i Qxi + j the WENO5 epsilon terms 3 eps ws^2 (C0, C1, C2) at [3 s + 0..2],
+//   ws = w^p_i w^xi_j / 2 (the limiter acts on the weight-normalised population)
 constexpr int TAB_PBAR = 0;
 constexpr int TAB_PBAR2 = QP_MAX;
 constexpr int TAB_WP = 2 * QP_MAX;
@@ -58,18 +60,21 @@ constexpr int TAB_K = 3 * QP_MAX;
 constexpr int TAB_XI = TAB_K + QP_MAX * (NP_MAX + 1);
 __host__ __device__ inline int tab_pw(int Qxi) { return TAB_XI + Qxi; }
 __host__ __device__ inline int tab_cxi(int Qxi) { return TAB_XI + Qxi + Qxi * (NV_MAX + 1); }
-inline int tab_size(int Qxi) { return tab_cxi(Qxi) + 3 * Qxi; }
+__host__ __device__ inline int tab_eps(int Qxi) { return tab_cxi(Qxi) + 3 * Qxi; }
+inline int tab_size(int Qp, int Qxi) { return tab_eps(Qxi) + 3 * Qp * Qxi; }
 // Per-tube FP32 tables of the reduced-precision path (floats, starting at TubeDev::tabf):
 //   [0, 2 QP_MAX)           pbar_i as a hi/lo float pair: hi at i, lo at QP_MAX + i
 //   [2 QP_MAX, 4 QP_MAX)    pbar_i^2 likewise
 //   then xi_j hi, xi_j lo, xi_j^2 hi, xi_j^2 lo (Qxi each)
-//   then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k], then b_st dt xi_j / dx at [st Qxi + j]
+//   then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k], then b_st dt xi_j / dx at [st Qxi + j], then the WENO5
+//   epsilon terms at [3 s + 0..2] as in the FP64 table
 constexpr int TABF_P1 = 0;
 constexpr int TABF_P2 = 2 * QP_MAX;
 constexpr int TABF_X = 4 * QP_MAX;
 __host__ __device__ inline int tabf_pw(int Qxi) { return TABF_X + 4 * Qxi; }
 __host__ __device__ inline int tabf_cxi(int Qxi) { return tabf_pw(Qxi) + Qxi * (NV_MAX + 1); }
-inline int tabf_size(int Qxi) { return tabf_cxi(Qxi) + 3 * Qxi; }
+__host__ __device__ inline int tabf_iws(int Qxi) { return tabf_cxi(Qxi) + 3 * Qxi; }
+inline int tabf_size(int Qp, int Qxi) { return tabf_iws(Qxi) + Qp * Qxi; }
 
 constexpr double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};  // Shu-Osher SSP-RK3: F_out = a F^n + b (F_in + dt L(F_in))
 constexpr double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};

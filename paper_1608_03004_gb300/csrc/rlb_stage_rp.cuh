@@ -64,6 +64,8 @@ struct StageArgsRP {
   float a, b;          // Shu-Osher combination F_out = a F^n + b (F_in + dt L(F_in))
   double bd;           // b in FP64 (for the collision rate)
   int stage;
+  int ntiles, schedule;  // as in the FP64 kernel
+  int* counter;
 };
 
 struct StageSmemRP {
@@ -197,8 +199,11 @@ __device__ void stage_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, St
         {
           const int p = c + (fwd ? 1 : 2);
           const float xd = row[p] - row[p - 1], yd = row[p + 1] - row[p];
+          // indicators of the weight-normalised differences (the squares of those of F would leave FP32's
+          // range for small weights); the combination is invariant under that common scale
+          const float iws = tabf[tabf_iws(Qxi) + s];
           float sa, sb, sc;
-          weno5_pair(xd, yd, fwd, sa, sb, sc);
+          weno5_pair(xd * iws, yd * iws, fwd, rlbdev::EPS_A, rlbdev::EPS_B, rlbdev::EPS_C, sa, sb, sc);
           sp0[c] = sa;
           sp1[c] = sb;
           sp2[c] = sc;
@@ -275,14 +280,16 @@ __device__ void stage_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, St
   }
 }
 
-template <typename S>
+template <typename S, int SCHED>
 __global__ void __launch_bounds__(NT) rlb_stage_rp_kernel(StageArgsRP A) {
   extern __shared__ __align__(16) unsigned char stage_rp_smem_raw[];
   StageSmemRP& sm = *reinterpret_cast<StageSmemRP*>(stage_rp_smem_raw);
-  const int2 tl = A.tiles[blockIdx.x];
-  const TubeDev T = A.tubes[tl.x];
-  if (T.Np == 2 && T.Nv == 5)
-    stage_tile_rp<S, 2, 5>(A, T, tl.y, sm);
-  else
-    stage_tile_rp<S, NP_MAX, NV_MAX>(A, T, tl.y, sm);
+  for_each_tile(A.ntiles, SCHED, A.counter, [&](int t) {
+    const int2 tl = A.tiles[t];
+    const TubeDev T = A.tubes[tl.x];
+    if (T.Np == 2 && T.Nv == 5)
+      stage_tile_rp<S, 2, 5>(A, T, tl.y, sm);
+    else
+      stage_tile_rp<S, NP_MAX, NV_MAX>(A, T, tl.y, sm);
+  });
 }
