@@ -50,9 +50,11 @@ BYTES_PER_NODE_STEP = 64
 PROFILES = {"f64": os.path.join(ROOT, "profiles", "rlb_stage_kernel_sod_sweep.md"),
             "f32": os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_f32_stress.md"),
             "bf16": os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_bf16_stress.md")}
-KERNEL_SRCS = {"f64": [os.path.join(ROOT, "paper_1608_03004_gb300", "csrc", "rlb.cu")],
-               "f32": [os.path.join(ROOT, "paper_1608_03004_gb300", "csrc", "rlb_stage_rp.cuh")],
-               "bf16": [os.path.join(ROOT, "paper_1608_03004_gb300", "csrc", "rlb_stage_rp.cuh")]}
+_CSRC = os.path.join(ROOT, "paper_1608_03004_gb300", "csrc")
+_SHARED = [os.path.join(_CSRC, "rlb_device_math.cuh"), os.path.join(_CSRC, "rlb_internal.h")]
+KERNEL_SRCS = {"f64": [os.path.join(_CSRC, "rlb.cu")] + _SHARED,
+               "f32": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED,
+               "bf16": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED}
 ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
 CPU_SAMPLE_NODES = 24_000_000  # bound on the velocity nodes the oracle advances per CPU sample step
 
