@@ -217,6 +217,61 @@ rlb_status rlb_autotune(rlb_handle h, int32_t trial_steps, rlb_launch *best, dou
 rlb_status rlb_step_static(const rlb_tube *tube, const double *F_in, double *F_out, int64_t nsteps,
                            int32_t *flag, void *stream);
 
+/* ---------------------------------------------------------------------------------------------------------
+ * Adjoint (reverse-mode gradient) of the time step. The paper has no adjoint; these entry points give the
+ * gradient of a scalar loss of the state after a run with respect to the initial state, the initial fields
+ * (P, n, v) and log(tau) of every tube, by the exact transpose of each stage of the discrete step (WENO5
+ * flux differences, Anderson-Witting collision with the equilibrium of Eq. (feqtrunc) through the Landau
+ * frame, SSP-RK3 combination) evaluated in FP64 on the GPU. The time step dt of a tube is held fixed.
+ * Handles with reduced-precision storage return RLB_EINVAL from all four.
+ * Layouts: "packed state" = the layout of rlb_get_state (per tube [Q][Nx] doubles, tube after tube);
+ * "field layout" = [sum of Nx] doubles, tube after tube. All pointers below are device pointers unless
+ * stated; the calls run on the handle's stream and return after their work has finished.
+ * --------------------------------------------------------------------------------------------------------- */
+
+/*
+ * rlb_record - advance every tube by nsteps steps as rlb_step does (bit-identical results), keeping a
+ *   checkpoint of the state every `every` steps (the state before steps 0, every, 2 every, ...) in device
+ *   memory owned by the handle; a later rlb_backward recomputes each segment of `every` steps from its
+ *   checkpoint. Replaces any earlier record. Memory: ceil(nsteps / every) states.
+ *   Returns RLB_EINVAL (nsteps < 1, every < 1, reduced storage), RLB_ENOMEM, RLB_ECUDA, or RLB_ENONPHYS if a
+ *   cell became non-physical during the run.
+ */
+rlb_status rlb_record(rlb_handle h, int64_t nsteps, int32_t every);
+
+/*
+ * rlb_backward - reverse sweep over the last rlb_record.
+ *   seed:         packed state, dL/dF of the state after the recorded steps (read only).
+ *   grad_state:   packed state, written with dL/dF of the state before the recorded steps; may be NULL.
+ *   grad_log_tau: HOST array [ntubes], written with dL/dlog(tau) of each tube (0 for tau = infinity); may be
+ *                 NULL.
+ *   The handle's state is not changed. Scratch: (3 every + 1) + 4 states, allocated on first use and kept
+ *   until rlb_destroy. Returns RLB_EINVAL (no record, reduced storage, seed NULL), RLB_ENOMEM, RLB_ECUDA,
+ *   RLB_ENONPHYS (a recomputed cell was non-physical).
+ */
+rlb_status rlb_backward(rlb_handle h, const double *seed, double *grad_state, double *grad_log_tau);
+
+/*
+ * rlb_moments_vjp - seed of rlb_backward from the adjoint of the five conserved moments:
+ *   grad_moments: [5][sum of Nx] (field layout per row: N^0, N^x, T^00, T^0x, T^xx, as rows 0..4 of
+ *                 rlb_moments), read only.
+ *   seed:         packed state, written with dL/dF_s(x) = sum_a dL/dM_a(x) c_a(s), c = (pbar, pbar xi,
+ *                 pbar^2, pbar^2 xi, pbar^2 xi^2) (the moment sums of the section "Relativistic lattice
+ *                 Boltzmann equation").
+ */
+rlb_status rlb_moments_vjp(rlb_handle h, const double *grad_moments, double *seed);
+
+/*
+ * rlb_init_vjp - adjoint of the initial condition of rlb_init (F = F^eq of Eq. (feqtrunc) with T = P/n and
+ *   beta = v in every cell): from dL/dF of that state to dL/dP, dL/dn, dL/dv.
+ *   P, n, v:           field layout, the initial fields given to rlb_init (read only).
+ *   grad_state:        packed state, dL/dF of the initial state (e.g. grad_state of rlb_backward).
+ *   grad_P, grad_n, grad_v: field layout, written.
+ *   Returns RLB_EINVAL for NULL pointers, reduced storage or a non-physical initial cell.
+ */
+rlb_status rlb_init_vjp(rlb_handle h, const double *P, const double *n, const double *v,
+                        const double *grad_state, double *grad_P, double *grad_n, double *grad_v);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,7 +2,8 @@
 model for massless particles (Blaga & Ambrus, arXiv:1608.03004).
 
 The compute path is the CUDA library ``librlb.so`` (sources in ``csrc/``, C ABI in ``include/rlb.h``);
-``binding`` exposes its entry points under the same names. ``workloads`` holds the seeded synthetic inputs.
+``binding`` exposes its entry points under the same names; ``adjoint.run_moments`` wraps the library's adjoint
+entry points in a torch.autograd.Function. ``workloads`` holds the seeded synthetic inputs.
 Importing this package loads nothing; the library is loaded on the first call and a missing library is an
 error, never a fallback.
 """
@@ -28,13 +29,17 @@ from .binding import (  # noqa: F401
     load,
     rlb_destroy,
     rlb_autotune,
+    rlb_backward,
     rlb_error_string,
     rlb_get_launch,
     rlb_get_state,
     rlb_init,
     rlb_init_riemann,
+    rlb_init_vjp,
     rlb_moments,
+    rlb_moments_vjp,
     rlb_quadrature,
+    rlb_record,
     rlb_set_launch,
     rlb_set_state,
     rlb_state_size,

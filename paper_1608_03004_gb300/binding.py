@@ -112,6 +112,10 @@ def load():
             "rlb_get_launch": ([vp, ctypes.POINTER(Launch)], ctypes.c_int),
             "rlb_set_launch": ([vp, ctypes.POINTER(Launch)], ctypes.c_int),
             "rlb_autotune": ([vp, ip, ctypes.POINTER(Launch), dp], ctypes.c_int),
+            "rlb_record": ([vp, ctypes.c_int64, ip], ctypes.c_int),
+            "rlb_backward": ([vp, vp, vp, dp], ctypes.c_int),
+            "rlb_moments_vjp": ([vp, vp, vp], ctypes.c_int),
+            "rlb_init_vjp": ([vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -338,3 +342,37 @@ def rlb_autotune(h: Handle, trial_steps: int = 3):
     ms = ctypes.c_double()
     _check(load().rlb_autotune(h.ptr, int(trial_steps), ctypes.byref(best), ctypes.byref(ms)), "rlb_autotune")
     return best, ms.value
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Adjoint (FP64 handles): device buffers are contiguous float64 CUDA tensors
+# ---------------------------------------------------------------------------------------------------------
+
+def rlb_record(h: Handle, nsteps: int, every: int) -> None:
+    """rlb_step(h, nsteps) keeping a checkpoint every `every` steps for rlb_backward."""
+    _check(load().rlb_record(h.ptr, int(nsteps), int(every)), "rlb_record")
+
+
+def rlb_backward(h: Handle, seed, grad_state=None):
+    """Reverse sweep over the last rlb_record. seed: dL/dF of the final state (packed, CUDA tensor).
+    Returns (grad_state tensor or None, numpy array of dL/dlog(tau) per tube)."""
+    glt = np.zeros(len(h.tubes))
+    gp = None if grad_state is None else _dev_ptr(grad_state, h.state_size)
+    _check(load().rlb_backward(h.ptr, _dev_ptr(seed, h.state_size), gp,
+                               glt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "rlb_backward")
+    return grad_state, glt
+
+
+def rlb_moments_vjp(h: Handle, grad_moments, seed):
+    """seed (packed, CUDA) = dL/dF from grad_moments [5][sum Nx] (CUDA): the adjoint of the five moments."""
+    _check(load().rlb_moments_vjp(h.ptr, _dev_ptr(grad_moments, 5 * h.nx_total), _dev_ptr(seed, h.state_size)),
+           "rlb_moments_vjp")
+    return seed
+
+
+def rlb_init_vjp(h: Handle, P, n, v, grad_state, grad_P, grad_n, grad_v) -> None:
+    """dL/dP, dL/dn, dL/dv of the initial fields (CUDA, field layout) from dL/dF of the initial state."""
+    m = h.nx_total
+    _check(load().rlb_init_vjp(h.ptr, _dev_ptr(P, m), _dev_ptr(n, m), _dev_ptr(v, m),
+                               _dev_ptr(grad_state, h.state_size), _dev_ptr(grad_P, m), _dev_ptr(grad_n, m),
+                               _dev_ptr(grad_v, m)), "rlb_init_vjp")

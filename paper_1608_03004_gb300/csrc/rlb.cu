@@ -556,6 +556,8 @@ __global__ void narrow_kernel(const double* src, S* dst, int ld, int Nx) {
   if (x < Nx) st_d<S>(dst + (size_t)r * ld + x, src[(size_t)r * Nx + x]);
 }
 
+#include "rlb_adjoint.cuh"
+
 // --------------------------------------------------------------------------------------------------
 // Host side
 // --------------------------------------------------------------------------------------------------
@@ -621,6 +623,10 @@ rlb_status ensure_series_tables(int dev) {
     RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmem)));
   for (const void* k : rp)
     RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmemRP)));
+  RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(AdjSmem)));
+  RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_init_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(InitVjpSmem)));
   g_tables_ready[dev] = true;
   return RLB_OK;
 }
@@ -657,6 +663,17 @@ struct rlb_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int* d_counters = nullptr;   // 3 per step, GRAPH_MAX steps
+  // adjoint: checkpoints of the last rlb_record, recompute and adjoint scratch, tiles of TXA cells
+  double* ckpt = nullptr;
+  long long ckpt_cap = 0;      // states allocated
+  int64_t rec_steps = 0;
+  int rec_every = 0;
+  double* seg = nullptr;
+  long long seg_cap = 0;       // states allocated
+  double* adj = nullptr;       // 4 states: adjoints of F^(n+1) / F^n, F^(1), F^(2) and the F^n accumulator
+  int2* d_atiles = nullptr;
+  std::vector<int> atile_tube;
+  double* d_dlt = nullptr;     // per adjoint tile: dL/dlog(tau)
 };
 
 namespace {
@@ -671,6 +688,11 @@ void free_ctx(rlb_ctx* h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   cudaFree(h->d_counters);
+  cudaFree(h->ckpt);
+  cudaFree(h->seg);
+  cudaFree(h->adj);
+  cudaFree(h->d_atiles);
+  cudaFree(h->d_dlt);
   cudaFree(h->d_tubes);
   cudaFree(h->d_tiles);
   cudaFree(h->d_tab);
@@ -782,6 +804,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     d.inv_tau = d.collide ? 1.0 / t.tau : 0.0;
     d.x_left = xleft ? xleft[b] : 0.0;
     d.index = b;
+    d.poff = h->packed;
     off += (long long)t.Qp * t.Qxi * d.ld;
     xoff += t.Nx;
     h->packed += (long long)t.Qp * t.Qxi * t.Nx;
@@ -1478,3 +1501,196 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
   }
   return cuda_status(cudaGetLastError());
 }
+
+// --------------------------------------------------------------------------------------------------
+// Adjoint: record with checkpoints, reverse sweep, seeds from the moments, initial-condition adjoint
+// --------------------------------------------------------------------------------------------------
+
+namespace {
+
+// One FP64 forward stage between explicit buffers (one CTA per tile; every launch shape gives the same bits).
+rlb_status launch_stage_ptrs(rlb_ctx* h, int st, const double* Fn, const double* Fin, double* Fout) {
+  StageArgs A{};
+  A.tubes = h->d_tubes;
+  A.tiles = h->d_tiles;
+  A.tab = h->d_tab;
+  A.flag = h->d_flag;
+  A.Fn = Fn;
+  A.Fin = Fin;
+  A.Fout = Fout;
+  A.a = RK_A[st];
+  A.b = RK_B[st];
+  A.stage = st;
+  A.ntiles = h->ntiles;
+  A.schedule = RLB_SCHED_TILE;
+  A.counter = h->d_counters;
+  rlb_stage_kernel<0><<<h->ntiles, NT, sizeof(StageSmem), h->stream>>>(A);
+  return cuda_status(cudaGetLastError());
+}
+
+rlb_status launch_adjoint(rlb_ctx* h, int st, int mode, const double* Fin, const double* mu, double* out,
+                          double* acc) {
+  AdjArgs A{};
+  A.tubes = h->d_tubes;
+  A.tiles = h->d_atiles;
+  A.Fin = Fin;
+  A.mu = mu;
+  A.out = out;
+  A.acc = acc;
+  A.tab = h->d_tab;
+  A.flag = h->d_flag;
+  A.dlt = h->d_dlt;
+  A.a = RK_A[st];
+  A.b = RK_B[st];
+  A.mode = mode;
+  rlb_adjoint_kernel<<<(int)h->atile_tube.size(), NT, sizeof(AdjSmem), h->stream>>>(A);
+  return cuda_status(cudaGetLastError());
+}
+
+// Tiles of TXA cells (tube after tube) and their dL/dlog(tau) accumulators.
+rlb_status ensure_adjoint_tiles(rlb_ctx* h) {
+  if (h->d_atiles) return RLB_OK;
+  std::vector<int2> tiles;
+  for (size_t b = 0; b < h->tubes.size(); ++b)
+    for (int x0 = 0; x0 < (int)h->tubes[b].Nx; x0 += TXA) {
+      tiles.push_back(make_int2((int)b, x0));
+      h->atile_tube.push_back((int)b);
+    }
+  RLB_CUDA(cudaMalloc(&h->d_atiles, sizeof(int2) * tiles.size()));
+  RLB_CUDA(cudaMalloc(&h->d_dlt, sizeof(double) * tiles.size()));
+  RLB_CUDA(cudaMemcpyAsync(h->d_atiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
+  RLB_CUDA(cudaStreamSynchronize(h->stream));  // the host vector goes out of scope
+  return RLB_OK;
+}
+
+// Packed <-> padded FP64 state of every tube (device to device).
+rlb_status packed_to_padded(rlb_ctx* h, const double* P, double* F) {
+  for (size_t b = 0; b < h->tubes.size(); ++b) {
+    const TubeDev& d = h->td[b];
+    RLB_CUDA(cudaMemcpy2DAsync(F + d.off, sizeof(double) * d.ld, P + d.poff, sizeof(double) * d.Nx,
+                               sizeof(double) * d.Nx, (size_t)d.Qp * d.Qxi, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return RLB_OK;
+}
+
+rlb_status padded_to_packed(rlb_ctx* h, const double* F, double* P) {
+  for (size_t b = 0; b < h->tubes.size(); ++b) {
+    const TubeDev& d = h->td[b];
+    RLB_CUDA(cudaMemcpy2DAsync(P + d.poff, sizeof(double) * d.Nx, F + d.off, sizeof(double) * d.ld,
+                               sizeof(double) * d.Nx, (size_t)d.Qp * d.Qxi, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return RLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rlb_status rlb_record(rlb_handle h, int64_t nsteps, int32_t every) {
+  if (!h || nsteps < 1 || every < 1 || h->storage != RLB_STORAGE_F64) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  h->rec_steps = 0;
+  const long long se = h->state_elems;
+  const long long nck = (nsteps + every - 1) / every;
+  if (h->ckpt_cap < nck) {
+    cudaFree(h->ckpt);
+    h->ckpt = nullptr;
+    h->ckpt_cap = 0;
+    RLB_CUDA(cudaMalloc(&h->ckpt, sizeof(double) * se * nck));
+    h->ckpt_cap = nck;
+  }
+  for (long long k = 0; k < nck; ++k) {
+    RLB_CUDA(cudaMemcpyAsync(h->ckpt + k * se, h->F, sizeof(double) * se, cudaMemcpyDeviceToDevice, h->stream));
+    const int64_t len = std::min<int64_t>(every, nsteps - k * every);
+    const rlb_status st = rlb_step(h, len);
+    if (st != RLB_OK) return st;
+  }
+  const rlb_status st = check_flag(h);
+  if (st != RLB_OK) return st;
+  h->rec_steps = nsteps;
+  h->rec_every = every;
+  return RLB_OK;
+}
+
+rlb_status rlb_backward(rlb_handle h, const double* seed, double* grad_state, double* grad_log_tau) {
+  if (!h || !seed || h->storage != RLB_STORAGE_F64 || h->rec_steps < 1) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  rlb_status st = ensure_adjoint_tiles(h);
+  if (st != RLB_OK) return st;
+  const long long se = h->state_elems;
+  const int every = h->rec_every;
+  if (h->seg_cap < 3LL * every + 1) {
+    cudaFree(h->seg);
+    h->seg = nullptr;
+    h->seg_cap = 0;
+    RLB_CUDA(cudaMalloc(&h->seg, sizeof(double) * se * (3LL * every + 1)));
+    h->seg_cap = 3LL * every + 1;
+  }
+  if (!h->adj) RLB_CUDA(cudaMalloc(&h->adj, sizeof(double) * se * 4));
+  double *L = h->adj, *L1 = L + se, *L2 = L1 + se, *LA = L2 + se;
+  RLB_CUDA(cudaMemsetAsync(h->adj, 0, sizeof(double) * se * 4, h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->d_dlt, 0, sizeof(double) * h->atile_tube.size(), h->stream));
+  st = packed_to_padded(h, seed, L);
+  if (st != RLB_OK) return st;
+  const long long nck = (h->rec_steps + every - 1) / every;
+  for (long long k = nck - 1; k >= 0; --k) {
+    const int64_t len = std::min<int64_t>(every, h->rec_steps - k * every);
+    double* S = h->seg;
+    RLB_CUDA(cudaMemcpyAsync(S, h->ckpt + k * se, sizeof(double) * se, cudaMemcpyDeviceToDevice, h->stream));
+    // recompute the segment, keeping the three stage inputs of every step
+    for (int64_t t = 0; t < len; ++t) {
+      double* Fn = S + 3 * t * se;
+      if ((st = launch_stage_ptrs(h, 0, Fn, Fn, Fn + se)) != RLB_OK) return st;
+      if ((st = launch_stage_ptrs(h, 1, Fn, Fn + se, Fn + 2 * se)) != RLB_OK) return st;
+      if ((st = launch_stage_ptrs(h, 2, Fn, Fn + 2 * se, Fn + 3 * se)) != RLB_OK) return st;
+    }
+    // reverse: stage 3, 2, 1 of every step, last step first
+    for (int64_t t = len - 1; t >= 0; --t) {
+      const double* Fn = S + 3 * t * se;
+      if ((st = launch_adjoint(h, 2, 2, Fn + 2 * se, L, L2, LA)) != RLB_OK) return st;
+      if ((st = launch_adjoint(h, 1, 1, Fn + se, L2, L1, LA)) != RLB_OK) return st;
+      if ((st = launch_adjoint(h, 0, 0, Fn, L1, L, LA)) != RLB_OK) return st;
+    }
+  }
+  if (grad_state) {
+    st = padded_to_packed(h, L, grad_state);
+    if (st != RLB_OK) return st;
+  }
+  std::vector<double> dl(h->atile_tube.size());
+  RLB_CUDA(cudaMemcpyAsync(dl.data(), h->d_dlt, sizeof(double) * dl.size(), cudaMemcpyDeviceToHost, h->stream));
+  st = check_flag(h);  // synchronises the stream
+  if (st != RLB_OK) return st;
+  if (grad_log_tau) {
+    for (size_t b = 0; b < h->tubes.size(); ++b) grad_log_tau[b] = 0.0;
+    for (size_t t = 0; t < dl.size(); ++t) grad_log_tau[h->atile_tube[t]] += dl[t];
+  }
+  return RLB_OK;
+}
+
+rlb_status rlb_moments_vjp(rlb_handle h, const double* grad_moments, double* seed) {
+  if (!h || !grad_moments || !seed || h->storage != RLB_STORAGE_F64) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  rlb_status st = ensure_adjoint_tiles(h);
+  if (st != RLB_OK) return st;
+  rlb_moments_vjp_kernel<<<(int)h->atile_tube.size(), NT, 0, h->stream>>>(h->d_tubes, h->d_atiles, h->d_tab,
+                                                                          grad_moments, h->nxtot, seed);
+  RLB_CUDA(cudaGetLastError());
+  RLB_CUDA(cudaStreamSynchronize(h->stream));
+  return RLB_OK;
+}
+
+rlb_status rlb_init_vjp(rlb_handle h, const double* P, const double* n, const double* v, const double* grad_state,
+                        double* grad_P, double* grad_n, double* grad_v) {
+  if (!h || !P || !n || !v || !grad_state || !grad_P || !grad_n || !grad_v || h->storage != RLB_STORAGE_F64)
+    return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  rlb_status st = ensure_adjoint_tiles(h);
+  if (st != RLB_OK) return st;
+  rlb_init_vjp_kernel<<<(int)h->atile_tube.size(), NT, sizeof(InitVjpSmem), h->stream>>>(
+      h->d_tubes, h->d_atiles, h->d_tab, P, n, v, grad_state, grad_P, grad_n, grad_v, h->d_flag);
+  RLB_CUDA(cudaGetLastError());
+  st = check_flag(h);
+  return st == RLB_ENONPHYS ? RLB_EINVAL : st;
+}
+
+}  // extern "C"

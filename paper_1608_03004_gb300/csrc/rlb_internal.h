@@ -40,6 +40,7 @@ struct TubeDev {
   int index;    // position of the tube in the caller's list
   int tabf;     // offset of this tube's FP32 tables (reduced-precision storage)
   int storage;  // RLB_STORAGE_F64 / F32 / BF16
+  long long poff;  // offset of this tube in the packed state layout (rows of Nx cells, tube after tube)
 };
 
 // Layout of one tube's tables (doubles, starting at TubeDev::tab):
