@@ -6,11 +6,16 @@ Nx = 4096, Qp = 3, tau in {1e-4, 1e-3, 1e-2, 1e-1, 1, 10, inf} x Qxi in {8, 32, 
 velocity nodes, all advanced together, one handle, FP64. A step is one SSP-RK3 time step of every tube
 (three launches of the stage kernel). One velocity-node update = one velocity at one cell over one step.
 
-    python bench.py [--steps K] [--warmup W] [--workload sweep|small|stress] [--precision f64|f32|bf16]
-                    [--impl ours|reference]
+    python bench.py [--steps K] [--warmup W] [--workload sweep|small|stress|batched|gradient|gradient_batch]
+                    [--precision f64|f32|bf16] [--impl ours|reference]
 
 --precision f32/bf16 stores F in that type (FP32 arithmetic, compensated moments reduced in FP64, FP64 Landau
 solve); its roofline is HBM (algorithmic 8 x element size bytes per velocity node per step).
+
+--workload gradient: one gradient of the inverse problem on Gaussian bumps (Nx = 2048, Q = 3 x 32, 1000 steps,
+tau = 0.08 against the T^00 profile of tau* = 0.05, checkpoints every 50 steps) with respect to log(tau) and the
+initial fields, through the adjoint; gradient_batch: 64 such tubes (bump seeds 4 .. 67) in one handle. A step
+is one gradient; one update = one velocity node carried one time step forward and back.
 
 Prints one JSON line. Under torchrun every rank advances its own copy of the workload (weak scaling, no
 collective on the data path); the time is the max over ranks.
@@ -47,16 +52,27 @@ FLOPS_PER_NODE_STAGE = 84
 # Algorithmic HBM bytes per velocity node per step with one launch per stage: stage inputs read once
 # (1 + 2 + 2 doubles), outputs written once (3 doubles).
 BYTES_PER_NODE_STEP = 64
-PROFILES = {"f64": os.path.join(ROOT, "profiles", "rlb_stage_kernel_sod_sweep.md"),
+PROFILES = {"adjoint": os.path.join(ROOT, "profiles", "rlb_adjoint_kernel_gradient.md"),
+            "f64": os.path.join(ROOT, "profiles", "rlb_stage_kernel_sod_sweep.md"),
             "f32": os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_f32_stress.md"),
             "bf16": os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_bf16_stress.md")}
 _CSRC = os.path.join(ROOT, "paper_1608_03004_gb300", "csrc")
 _SHARED = [os.path.join(_CSRC, "rlb_device_math.cuh"), os.path.join(_CSRC, "rlb_internal.h")]
-KERNEL_SRCS = {"f64": [os.path.join(_CSRC, "rlb.cu")] + _SHARED,
+KERNEL_SRCS = {"adjoint": [os.path.join(_CSRC, "rlb_adjoint.cuh")] + _SHARED,
+               "f64": [os.path.join(_CSRC, "rlb.cu")] + _SHARED,
                "f32": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED,
                "bf16": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED}
 ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
 CPU_SAMPLE_NODES = 24_000_000  # bound on the velocity nodes the oracle advances per CPU sample step
+GRAD_METRIC = "G velocity-node gradient updates/s"
+GRAD_UNIT = "G gradient updates/s"
+GRAD_STEPS, GRAD_EVERY, GRAD_TAU, GRAD_TAU_STAR = 1000, 50, 0.08, 0.05
+# Algorithmic FP64 flops per velocity node per adjoint stage (FMA = 2, a division counted as one flop):
+# WENO5 interface derivative 130 (candidates 16, indicator terms 18, eps + beta_k 18, alpha_k and weights 11,
+# Phi 5, kappa_k 12, their products with the indicator terms 12, the five partials 38), adjoint flux 3, slot
+# products 5, gather 4, collision and moment weights 15, output 5, equilibrium and the Lam / S0 / S1 sums 33,
+# moments 6.
+ADJ_FLOPS_PER_NODE_STAGE = 201
 
 
 def workload(name: str, nx: int | None = None):
@@ -72,6 +88,14 @@ def workload(name: str, nx: int | None = None):
         return W.batched_tubes(), ("256 shock tubes, seed 160803004: Nx ~ U[1024,16384], log10 tau ~ U[-4,1], "
                                    "Qxi in {8,16,32,64}, Qp=3, P_L ~ U[0.5,2], P_R = P_L U(0.01,0.5), "
                                    "dt=min(0.5dx,0.45tau), open BC")
+    if name == "gradient":
+        return [W.gaussian_bumps(tau=GRAD_TAU)], ("inverse problem on Gaussian bumps: Nx=2048, Qp=3, Qxi=32, "
+                                                  "Np=2, Nv=5, dt=0.5dx, open BC, tau=0.08 against the T00 profile "
+                                                  "of tau*=0.05, 1000 steps, checkpoints every 50")
+    if name == "gradient_batch":
+        return [W.gaussian_bumps(tau=GRAD_TAU, seed=4 + k) for k in range(64)], (
+            "64 inverse problems on Gaussian bumps (seeds 4..67): Nx=2048, Qp=3, Qxi=32, Np=2, Nv=5, dt=0.5dx, "
+            "open BC, tau=0.08 against the T00 profiles of tau*=0.05, 1000 steps, checkpoints every 50")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -298,8 +322,60 @@ def rank_prints(rank: int) -> bool:
 # arms
 # ---------------------------------------------------------------------------------------------------------
 
+def _oracle_fd_gradient_task(spec, nsteps: int) -> float:
+    """Seconds for the oracle's central-difference dL/dlog(tau) of one tube over nsteps (two forward runs at
+    tau exp(+-h), dt fixed, then the loss)."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    from oracle import gradient as og
+
+    p = oracle.params(Qp=spec.Qp, Qxi=spec.Qxi, Np=spec.Np, Nv=spec.Nv, Nx=spec.Nx, dx=spec.dx, dt=spec.dt,
+                      tau=spec.tau, bc=spec.bc)
+    t0 = time.perf_counter()
+    og.grad_log_tau(p, spec.P, spec.n, spec.v, nsteps, lambda m: 0.5 * float(np.sum(m[2] ** 2)))
+    return time.perf_counter() - t0
+
+
+def oracle_gradient_sample(specs, nsteps: int):
+    """The oracle's gradient (central differences in log tau) on up to one tube per host core for nsteps steps;
+    returns (G gradient updates/s, cores, description)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    oracle.build()
+    cores = host_cores()
+    sample = specs[:max(1, min(len(specs), cores))]
+    with cf.ProcessPoolExecutor(max_workers=len(sample), mp_context=mp.get_context("spawn")) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(_oracle_fd_gradient_task, sample, [nsteps] * len(sample)))
+        wall = time.perf_counter() - t0
+    nodes = W.total_nodes(sample)
+    what = (f"dL/dlog(tau) by central differences of the plain C FP64 oracle (two forward runs of {nsteps} "
+            f"steps) on {len(sample)} of the workload's tubes ({nodes} velocity nodes), one process per tube")
+    return nodes * nsteps / wall / 1e9, len(sample), what
+
+
 def run_reference(args, specs, desc, rank):
     if not rank_prints(rank):  # under torchrun only rank 0 runs the CPU reference
+        return
+    if args.workload.startswith("gradient"):
+        vals = []
+        for k in range(args.warmup + args.steps):
+            val, cores, what = oracle_gradient_sample(specs, 10)
+            if k >= args.warmup:
+                vals.append(val)
+        value = statistics.mean(vals)
+        nodes = W.total_nodes(specs)
+        line = {"impl": "reference", "metric": GRAD_METRIC, "value": value, "unit": GRAD_UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * nodes * GRAD_STEPS / (value * 1e9), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": desc, "velocity_nodes": nodes},
+                "cpu_baseline": {"value": value, "unit": GRAD_UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"each step: {what}"},
+                "e2e": {"value": value, "unit": GRAD_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     specs, what = cpu_sample(specs)
     pool = OraclePool(specs, host_cores())
@@ -439,13 +515,142 @@ def run_ours(args, specs, desc, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_gradient(args, specs, desc, rank, world):
+    """Gradients of the inverse problem through the adjoint: each step is one full gradient (set the initial
+    state, rlb_record, the loss's seed, rlb_backward, rlb_init_vjp)."""
+    import torch
+
+    from paper_1608_03004_gb300 import adjoint
+    from paper_1608_03004_gb300 import binding as rb
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    f64 = dict(dtype=torch.float64, device="cuda")
+    mk = lambda s, tau: rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, tau, s.bc, rb.STORAGE_F64)  # noqa: E731
+    tubes = [mk(s, GRAD_TAU) for s in specs]
+    P, n, v = (np.concatenate([getattr(s, a) for s in specs]) for a in ("P", "n", "v"))
+    Pd, nd, vd = (torch.tensor(a, **f64) for a in (P, n, v))
+    nodes = W.total_nodes(specs)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with rb.rlb_init([mk(s, GRAD_TAU_STAR) for s in specs], Pd, nd, vd) as hs:  # the target profiles
+        rb.rlb_step(hs, GRAD_STEPS)
+        ft = torch.empty((rb.NFIELDS, hs.nx_total), **f64)
+        rb.rlb_moments(hs, ft)
+        target = ft[2].clone()
+    h = rb.rlb_init(tubes, Pd, nd, vd)
+    F0 = torch.empty(h.state_size, **f64)
+    rb.rlb_get_state(h, F0)
+    fields = torch.empty((rb.NFIELDS, h.nx_total), **f64)
+    gm = torch.zeros((5, h.nx_total), **f64)
+    seed, gF = torch.empty(h.state_size, **f64), torch.empty(h.state_size, **f64)
+    gP, gn, gv = (torch.empty(h.nx_total, **f64) for _ in range(3))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+
+    def gradient(e=None):
+        rb.rlb_set_state(h, F0)
+        if e:
+            e[0].record(stream)
+        rb.rlb_record(h, GRAD_STEPS, GRAD_EVERY)
+        if e:
+            e[1].record(stream)
+        rb.rlb_moments(h, fields)
+        torch.sub(fields[2], target, out=gm[2])  # dL/dT^00 of L = 1/2 sum (T^00 - target)^2
+        rb.rlb_moments_vjp(h, gm, seed)
+        if e:
+            e[2].record(stream)
+        _, glt = rb.rlb_backward(h, seed, gF)
+        if e:
+            e[3].record(stream)
+        rb.rlb_init_vjp(h, Pd, nd, vd, gF, gP, gn, gv)
+        if e:
+            e[4].record(stream)
+        return glt
+
+    for _ in range(args.warmup):
+        gradient()
+    torch.cuda.synchronize()
+    barrier()
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    clocks = ClockSampler(int(visible[dev]) if dev < len(visible) and visible[dev].isdigit() else dev)
+    for k in range(args.steps):
+        glt = gradient(ev[k])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    total_ms = sum(e[0].elapsed_time(e[4]) for e in ev)
+    record_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    backward_ms = sum(e[2].elapsed_time(e[3]) for e in ev)
+    total_ms, record_ms, backward_ms = reduce_max_over_ranks([total_ms, record_ms, backward_ms], world)
+    # the reverse sweep recomputes the recorded forward launches, then runs 3 GRAD_STEPS adjoint launches
+    adj_launch_ms = max(backward_ms - record_ms, 1e-9) / (3 * GRAD_STEPS * args.steps)
+
+    # end to end: the autograd call from host arrays (pinned H2D of P, n, v; D2H of the four gradients)
+    e2e_steps = max(2, min(args.steps, 3))
+    Ph, nh, vh = (torch.from_numpy(a).pin_memory() for a in (P, n, v))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lt = torch.full((len(tubes),), math.log(GRAD_TAU), dtype=torch.float64, requires_grad=True)
+        Pt, nt, vt = (a.to("cuda", non_blocking=True).requires_grad_() for a in (Ph, nh, vh))
+        M = adjoint.run_moments(lt, Pt, nt, vt, tubes, GRAD_STEPS, GRAD_EVERY)
+        (0.5 * ((M[2] - target) ** 2).sum()).backward()
+        grads = [lt.grad.numpy(), Pt.grad.cpu().numpy(), nt.grad.cpu().numpy(), vt.grad.cpu().numpy()]
+    e2e_s = reduce_max_over_ranks([time.perf_counter() - t0], world)[0]
+    rb.rlb_destroy(h)
+    assert all(np.all(np.isfinite(g)) for g in grads) and np.all(np.isfinite(glt))
+
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    fp64_peak = props.multi_processor_count * 4 * sm_max * 1e6 / 1e12
+    achieved = ADJ_FLOPS_PER_NODE_STAGE * nodes / (adj_launch_ms * 1e-3) / 1e12
+    tiles = sum((s.Nx + 59) // 60 for s in specs)
+    line = {
+        "metric": GRAD_METRIC, "value": whole_job_rate(nodes, GRAD_STEPS * args.steps, world, total_ms * 1e-3),
+        "unit": GRAD_UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "velocity_nodes": nodes, "tubes": len(specs),
+                   "step": "one gradient: record 1000 steps with checkpoints, seed, reverse sweep (recompute + "
+                           "adjoint), initial-condition adjoint",
+                   "record_ms_per_step": record_ms / args.steps, "backward_ms_per_step": backward_ms / args.steps,
+                   "adjoint_ctas_per_launch": tiles,
+                   "l2": "state %.1f MB per buffer; checkpoints and the recomputed segment %.0f MB; no flush"
+                         % (8 * nodes / 1e6, 8 * nodes * (GRAD_STEPS // GRAD_EVERY + 3 * GRAD_EVERY + 1) / 1e6),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak,
+                     "traffic": ncu_traffic_per_launch("adjoint", args.workload), "kernel": "rlb_adjoint_kernel",
+                     "launch_ms": adj_launch_ms,
+                     "note": f"{ADJ_FLOPS_PER_NODE_STAGE} algorithmic FP64 flops per velocity node per adjoint "
+                             "stage; launch time = (reverse sweep - record) / adjoint launches; peak = SMs x 2 "
+                             "DFMA/clk x 2 flops x max SM clock (derived)"},
+        "e2e": {"value": whole_job_rate(nodes, GRAD_STEPS * e2e_steps, world, e2e_s), "unit": GRAD_UNIT,
+                "h2d_bytes_per_step": 3 * 8 * h.nx_total, "d2h_bytes_per_step": 3 * 8 * h.nx_total + 8 * len(tubes),
+                "steps": e2e_steps, "api": "adjoint.run_moments (torch.autograd) from pinned host fields, "
+                                          "gradients read back"},
+        "clocks": clk,
+        "gpu_launches": 9 * GRAD_STEPS + 3,
+    }
+    if rank_prints(rank) and not args.no_cpu_baseline:
+        val, cores, what = oracle_gradient_sample(specs, 10)
+        line["cpu_baseline"] = {"value": val, "unit": GRAD_UNIT, "cores": cores, "kind": "oracle", "sample": what}
+    if rank_prints(rank):
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None, help="default 200; 5 for the gradient workloads")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "small", "stress", "batched"], default="sweep")
+    ap.add_argument("--workload", choices=["sweep", "small", "stress", "batched", "gradient", "gradient_batch"],
+                    default="sweep")
     ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default=None,
                     help="default f64; f32 for the batched workload (FP32 storage, FP64 moments)")
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with rlb_autotune first "
@@ -453,6 +658,8 @@ def main():
     ap.add_argument("--nx", type=int, default=None, help="cells of the stress tube (default 1048576)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5 if args.workload.startswith("gradient") else 200
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.precision is None:
@@ -474,7 +681,10 @@ def main():
     else:
         torch.cuda.set_device(0)
     try:
-        run_ours(args, specs, desc, rank, world)
+        if args.workload.startswith("gradient"):
+            run_gradient(args, specs, desc, rank, world)
+        else:
+            run_ours(args, specs, desc, rank, world)
     finally:
         if world > 1:
             torch.distributed.destroy_process_group()

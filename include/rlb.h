@@ -161,6 +161,10 @@ rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double *pbar, double *wp, dou
  *                 being captured by the caller always launch directly. 1 <= graph_steps <= 64 otherwise.
  *   order:        tile order, RLB_ORDER_COST (most expensive tubes first, the default) or RLB_ORDER_INTERLEAVE
  *                 (tubes interleaved tile by tile).
+ *   split:        work items per tile of the FP64 stage kernel: item k advances velocity rows [k Q / split,
+ *                 (k + 1) Q / split) of the tile after reducing its moments over all rows. 0 (the default)
+ *                 chooses: one item per tile when the tiles fill the GPU's resident CTA slots, else
+ *                 min(8, slots / tiles). 1 <= split <= 8 fixes it. Handles with reduced storage use one.
  */
 enum { RLB_SCHED_TILE = 0, RLB_SCHED_STRIDE = 1, RLB_SCHED_COUNTER = 2 };
 enum { RLB_ORDER_COST = 0, RLB_ORDER_INTERLEAVE = 1 };
@@ -169,6 +173,7 @@ typedef struct {
   int32_t ctas_per_sm;
   int32_t graph_steps;
   int32_t order;
+  int32_t split;
 } rlb_launch;
 
 /* rlb_get_launch / rlb_set_launch - read or change the launch shape (RLB_EINVAL for values out of range). */
@@ -177,7 +182,7 @@ rlb_status rlb_set_launch(rlb_handle h, const rlb_launch *cfg);
 
 /*
  * rlb_autotune - time every launch shape (schedules x ctas_per_sm in {occupancy, 1, 2} x both tile orders x
- *   graph on/off) for trial_steps steps on the handle's own tubes and state, keep the fastest. The state is
+ *   graph on/off x split automatic or 1 where the automatic choice is not 1) for trial_steps steps on the handle's own tubes and state, keep the fastest. The state is
  *   saved first and restored after every trial, so the handle's state is unchanged on return. best and
  *   best_ms_per_step (either may be NULL) receive the choice and its time per step. Synchronous.
  */

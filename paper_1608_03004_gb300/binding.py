@@ -67,7 +67,7 @@ class Launch(ctypes.Structure):
     """rlb_launch: scheduling of a handle's steps (never changes results)."""
 
     _fields_ = [("schedule", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
-                ("order", ctypes.c_int32)]
+                ("order", ctypes.c_int32), ("split", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

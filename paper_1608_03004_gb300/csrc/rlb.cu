@@ -63,6 +63,8 @@ struct StageArgs {
   int ntiles;         // tiles of this launch
   int schedule;       // 0: one CTA per tile; 1: persistent, grid stride; 2: persistent, work counter
   int* counter;       // work counter of schedule 2 (zeroed before the launch)
+  int split;          // work items per tile (<= 1: one): item k of a tile advances velocity rows
+                      // [k Q / split, (k + 1) Q / split) after reducing the moments over all rows
 };
 
 // Tile loop of a stage launch. Schedule 0 gives each CTA one tile; the persistent schedules keep a grid of
@@ -244,7 +246,7 @@ struct StageSmem {
 };
 
 template <int NPc, int NVc>
-__device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSmem& sm) {
+__device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int part, int nparts, StageSmem& sm) {
   const int tid = threadIdx.x, c = tid % GW, g = tid / GW;
   const double* tab = A.tab + T.tab;
   const int Qp = T.Qp, Qxi = T.Qxi, Q = Qp * Qxi, Nx = T.Nx, ld = T.ld;
@@ -316,9 +318,10 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, StageSm
   double* sp2 = sm.sp[g][2];
   double* phi = sm.phi[g];
   int buf = 0;
-  for (int s0 = 0; s0 < Q; s0 += NG, buf ^= 1) {
+  const int r_end = (part + 1) * Q / nparts;
+  for (int s0 = part * Q / nparts; s0 < r_end; s0 += NG, buf ^= 1) {
     const int s = s0 + g;
-    const bool rv = s < Q;
+    const bool rv = s < r_end;
     const int i = rv ? s / Qxi : 0, j = rv ? s - i * Qxi : 0;
     double* row = sm.row[buf][g];
     if (rv) {
@@ -383,13 +386,15 @@ template <int SCHED>
 __global__ void __launch_bounds__(NT, 4) rlb_stage_kernel(StageArgs A) {
   extern __shared__ __align__(16) unsigned char stage_smem_raw[];
   StageSmem& sm = *reinterpret_cast<StageSmem*>(stage_smem_raw);
-  for_each_tile(A.ntiles, SCHED, A.counter, [&](int t) {
+  const int K = A.split > 1 ? A.split : 1;
+  for_each_tile(A.ntiles * K, SCHED, A.counter, [&](int item) {
+    const int t = item / K, part = item - t * K;
     const int2 tl = A.tiles[t];
     const TubeDev T = A.tubes[tl.x];
     if (T.Np == 2 && T.Nv == 5)
-      stage_tile<2, 5>(A, T, tl.y, sm);
+      stage_tile<2, 5>(A, T, tl.y, part, K, sm);
     else
-      stage_tile<NP_MAX, NV_MAX>(A, T, tl.y, sm);
+      stage_tile<NP_MAX, NV_MAX>(A, T, tl.y, part, K, sm);
   });
 }
 
@@ -656,8 +661,11 @@ struct rlb_ctx {
   int* d_flag = nullptr;
   int* h_flag = nullptr;       // pinned
   // launch shape, CUDA graph of graph_steps steps, work counters of the counter schedule
-  rlb_launch cfg = {RLB_SCHED_TILE, 0, 0, RLB_ORDER_COST};
+  rlb_launch cfg = {RLB_SCHED_TILE, 0, 0, RLB_ORDER_COST, 0};
   int occupancy = 1;           // resident CTAs per SM of the stage kernel
+  int split = 1;               // automatic FP64 stage work items per tile (several when the tiles cannot fill
+                               // the GPU); rlb_launch.split overrides it
+  int asplit = 1;              // adjoint work items per adjoint tile
   int nsm = 1;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -679,6 +687,13 @@ struct rlb_ctx {
 namespace {
 
 constexpr int GRAPH_MAX = 64;  // longest captured graph, in steps
+constexpr int SPLIT_MAX = 8;   // most work items per tile
+
+// Work items per tile of the FP64 stage kernel for the handle's launch shape.
+int eff_split(const rlb_ctx* h) {
+  if (h->storage != RLB_STORAGE_F64) return 1;
+  return h->cfg.split > 0 ? h->cfg.split : h->split;
+}
 
 void free_ctx(rlb_ctx* h) {
   if (!h) return;
@@ -902,6 +917,10 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_rp_kernel<__nv_bfloat16, 1>, NT,
                                                            sizeof(StageSmemRP)));
   if (h->occupancy < 1) h->occupancy = 1;
+  // a handle whose tiles cannot fill the resident slots splits each tile's velocity rows over several CTAs
+  const long long slots = (long long)h->nsm * h->occupancy;
+  if (h->storage == RLB_STORAGE_F64 && h->ntiles < slots)
+    h->split = (int)std::min<long long>(SPLIT_MAX, slots / h->ntiles);
   return RLB_OK;
 }
 
@@ -1023,10 +1042,12 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
   const void* in[3] = {h->F, h->F1, h->F2};
   void* out[3] = {h->F1, h->F2, h->F};
   const int sched = h->cfg.schedule;
+  const int split = eff_split(h);
+  const int items = h->ntiles * split;
   const int grid = sched == RLB_SCHED_TILE
-                       ? h->ntiles
-                       : std::max(1, std::min(h->ntiles, h->nsm * (h->cfg.ctas_per_sm > 0 ? h->cfg.ctas_per_sm
-                                                                                          : h->occupancy)));
+                       ? items
+                       : std::max(1, std::min(items, h->nsm * (h->cfg.ctas_per_sm > 0 ? h->cfg.ctas_per_sm
+                                                                                       : h->occupancy)));
   if (sched == RLB_SCHED_COUNTER && in_graph)
     RLB_CUDA(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 3 * nsteps, stream));
   for (int64_t t = 0; t < nsteps; ++t) {
@@ -1048,6 +1069,7 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
         A.ntiles = h->ntiles;
         A.schedule = sched;
         A.counter = ctr + st;
+        A.split = split;
         if (sched == RLB_SCHED_TILE)
           rlb_stage_kernel<0><<<grid, NT, sizeof(StageSmem), stream>>>(A);
         else if (sched == RLB_SCHED_STRIDE)
@@ -1152,7 +1174,8 @@ rlb_status rlb_set_launch(rlb_handle h, const rlb_launch* cfg) {
   if (!h || !cfg) return RLB_EINVAL;
   if (cfg->schedule < RLB_SCHED_TILE || cfg->schedule > RLB_SCHED_COUNTER || cfg->ctas_per_sm < 0 ||
       cfg->ctas_per_sm > 64 || cfg->graph_steps < 0 || cfg->graph_steps > GRAPH_MAX ||
-      (cfg->order != RLB_ORDER_COST && cfg->order != RLB_ORDER_INTERLEAVE))
+      (cfg->order != RLB_ORDER_COST && cfg->order != RLB_ORDER_INTERLEAVE) || cfg->split < 0 ||
+      cfg->split > SPLIT_MAX)
     return RLB_EINVAL;
   DeviceGuard gd(h->dev);
   if (cfg->order != h->cfg.order) {
@@ -1190,25 +1213,27 @@ rlb_status rlb_autotune(rlb_handle h, int32_t trial_steps, rlb_launch* best, dou
   rlb_status st = cuda_status(e);
   const int scheds[7][2] = {{RLB_SCHED_TILE, 0}, {RLB_SCHED_STRIDE, 0}, {RLB_SCHED_STRIDE, 1}, {RLB_SCHED_STRIDE, 2},
                             {RLB_SCHED_COUNTER, 0}, {RLB_SCHED_COUNTER, 1}, {RLB_SCHED_COUNTER, 2}};
+  const int nsplit = (h->storage == RLB_STORAGE_F64 && h->split > 1) ? 2 : 1;  // automatic, and 1 if different
   for (int order = 0; order < 2 && st == RLB_OK; ++order)
     for (int k = 0; k < 7 && st == RLB_OK; ++k)
-      for (int graph = 0; graph < 2 && st == RLB_OK; ++graph) {
-        const rlb_launch c = {scheds[k][0], scheds[k][1], graph ? trial_steps : 0, order};
-        st = rlb_set_launch(h, &c);
-        if (st == RLB_OK) st = rlb_step(h, trial_steps);  // warm-up (and graph capture)
-        if (st == RLB_OK) st = cuda_status(restore());
-        if (st == RLB_OK) st = cuda_status(cudaEventRecord(t0, h->stream));
-        if (st == RLB_OK) st = rlb_step(h, trial_steps);
-        if (st == RLB_OK) st = cuda_status(cudaEventRecord(t1, h->stream));
-        if (st == RLB_OK) st = cuda_status(cudaEventSynchronize(t1));
-        float ms = 0.0f;
-        if (st == RLB_OK) st = cuda_status(cudaEventElapsedTime(&ms, t0, t1));
-        if (st == RLB_OK && (win_ms < 0.0f || ms < win_ms)) {
-          win_ms = ms;
-          win = c;
+      for (int graph = 0; graph < 2 && st == RLB_OK; ++graph)
+        for (int sp = 0; sp < nsplit && st == RLB_OK; ++sp) {
+          const rlb_launch c = {scheds[k][0], scheds[k][1], graph ? trial_steps : 0, order, sp};
+          st = rlb_set_launch(h, &c);
+          if (st == RLB_OK) st = rlb_step(h, trial_steps);  // warm-up (and graph capture)
+          if (st == RLB_OK) st = cuda_status(restore());
+          if (st == RLB_OK) st = cuda_status(cudaEventRecord(t0, h->stream));
+          if (st == RLB_OK) st = rlb_step(h, trial_steps);
+          if (st == RLB_OK) st = cuda_status(cudaEventRecord(t1, h->stream));
+          if (st == RLB_OK) st = cuda_status(cudaEventSynchronize(t1));
+          float ms = 0.0f;
+          if (st == RLB_OK) st = cuda_status(cudaEventElapsedTime(&ms, t0, t1));
+          if (st == RLB_OK && (win_ms < 0.0f || ms < win_ms)) {
+            win_ms = ms;
+            win = c;
+          }
+          if (st == RLB_OK) st = cuda_status(restore());
         }
-        if (st == RLB_OK) st = cuda_status(restore());
-      }
   if (st == RLB_OK) st = rlb_set_launch(h, &win);
   else rlb_set_launch(h, &start);
   if (t0) cudaEventDestroy(t0);
@@ -1524,7 +1549,8 @@ rlb_status launch_stage_ptrs(rlb_ctx* h, int st, const double* Fn, const double*
   A.ntiles = h->ntiles;
   A.schedule = RLB_SCHED_TILE;
   A.counter = h->d_counters;
-  rlb_stage_kernel<0><<<h->ntiles, NT, sizeof(StageSmem), h->stream>>>(A);
+  A.split = eff_split(h);
+  rlb_stage_kernel<0><<<h->ntiles * A.split, NT, sizeof(StageSmem), h->stream>>>(A);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1543,7 +1569,8 @@ rlb_status launch_adjoint(rlb_ctx* h, int st, int mode, const double* Fin, const
   A.a = RK_A[st];
   A.b = RK_B[st];
   A.mode = mode;
-  rlb_adjoint_kernel<<<(int)h->atile_tube.size(), NT, sizeof(AdjSmem), h->stream>>>(A);
+  A.split = h->asplit;
+  rlb_adjoint_kernel<<<(int)h->atile_tube.size() * h->asplit, NT, sizeof(AdjSmem), h->stream>>>(A);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1560,6 +1587,10 @@ rlb_status ensure_adjoint_tiles(rlb_ctx* h) {
   RLB_CUDA(cudaMalloc(&h->d_dlt, sizeof(double) * tiles.size()));
   RLB_CUDA(cudaMemcpyAsync(h->d_atiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
   RLB_CUDA(cudaStreamSynchronize(h->stream));  // the host vector goes out of scope
+  int occ = 1;
+  RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rlb_adjoint_kernel, NT, sizeof(AdjSmem)));
+  const long long slots = (long long)h->nsm * std::max(occ, 1);
+  if ((long long)tiles.size() < slots) h->asplit = (int)std::min<long long>(8, slots / (long long)tiles.size());
   return RLB_OK;
 }
 

@@ -36,6 +36,8 @@ struct AdjArgs {
   double a, b;        // the forward stage's Shu-Osher coefficients
   int mode;           // 2: out = b(mu + dt J^T mu), acc = a mu; 1: the same with acc += a mu;
                       // 0: out = acc + b(mu + dt J^T mu)
+  int split;          // CTAs per tile (<= 1: one): CTA k of a tile writes velocity rows
+                      // [k Q / split, (k + 1) Q / split) after the per-cell reductions over all rows
 };
 
 // Legendre coefficients and their beta derivatives (m = 2 .. Np+2, k <= Nv) of the tile's cells
@@ -237,23 +239,25 @@ __device__ __forceinline__ int wrap_cell(int p, int Nx) {
 // Phi = sum_k w_k q_k, w_k = alpha_k / sum alpha, alpha_k = d_k / (eps + beta_k)^2:
 //   dPhi/dv = sum_k w_k dq_k/dv + sum_k kappa_k dbeta_k/dv,  kappa_k = -2 w_k (q_k - Phi) / (eps + beta_k).
 __device__ void weno5_grad(const double v[5], double eps, double dP[5]) {
-  const double q0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
-  const double q1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
-  const double q2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+  constexpr double S6 = 1.0 / 6.0;
+  const double q0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) * S6;
+  const double q1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) * S6;
+  const double q2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) * S6;
   const double a0 = v[0] - 2.0 * v[1] + v[2], b0 = v[0] - 4.0 * v[1] + 3.0 * v[2];
   const double a1 = v[1] - 2.0 * v[2] + v[3], b1 = v[1] - v[3];
   const double a2 = v[2] - 2.0 * v[3] + v[4], b2 = 3.0 * v[2] - 4.0 * v[3] + v[4];
   const double e0 = eps + (13.0 / 12.0 * a0 * a0 + 0.25 * b0 * b0);
   const double e1 = eps + (13.0 / 12.0 * a1 * a1 + 0.25 * b1 * b1);
   const double e2 = eps + (13.0 / 12.0 * a2 * a2 + 0.25 * b2 * b2);
-  // alpha_k and the normalised weights
-  const double s0 = 0.1 / (e0 * e0), s1 = 0.6 / (e1 * e1), s2 = 0.3 / (e2 * e2);
-  const double sum = s0 + s1 + s2;
-  const double w0 = s0 / sum, w1 = s1 / sum, w2 = s2 / sum;
+  // alpha_k and the normalised weights, with the refined hardware reciprocal of the forward kernel
+  const double i0 = rlbdev::rcp_nr(e0), i1 = rlbdev::rcp_nr(e1), i2 = rlbdev::rcp_nr(e2);
+  const double s0 = 0.1 * i0 * i0, s1 = 0.6 * i1 * i1, s2 = 0.3 * i2 * i2;
+  const double is = rlbdev::rcp_nr(s0 + s1 + s2);
+  const double w0 = s0 * is, w1 = s1 * is, w2 = s2 * is;
   const double Phi = w0 * q0 + w1 * q1 + w2 * q2;
-  const double k0 = -2.0 * w0 * (q0 - Phi) / e0;
-  const double k1 = -2.0 * w1 * (q1 - Phi) / e1;
-  const double k2 = -2.0 * w2 * (q2 - Phi) / e2;
+  const double k0 = -2.0 * w0 * (q0 - Phi) * i0;
+  const double k1 = -2.0 * w1 * (q1 - Phi) * i1;
+  const double k2 = -2.0 * w2 * (q2 - Phi) * i2;
   // dbeta_k/dv = 13/6 a_k da_k/dv + 1/2 b_k db_k/dv
   const double A0 = 13.0 / 6.0 * k0 * a0, B0 = 0.5 * k0 * b0;
   const double A1 = 13.0 / 6.0 * k1 * a1, B1 = 0.5 * k1 * b1;
@@ -266,7 +270,8 @@ __device__ void weno5_grad(const double v[5], double eps, double dP[5]) {
 }
 
 template <int NPc, int NVc>
-__device__ void adjoint_tile(const AdjArgs& A, const TubeDev& T, int x0, AdjSmem& sm) {
+__device__ void adjoint_tile(const AdjArgs& A, const TubeDev& T, int tile, int x0, int part, int nparts,
+                             AdjSmem& sm) {
   const int tid = threadIdx.x, c = tid % GW, g = tid / GW;
   const double* tab = A.tab + T.tab;
   const int Qp = T.Qp, Qxi = T.Qxi, Q = Qp * Qxi, Nx = T.Nx, ld = T.ld;
@@ -392,10 +397,10 @@ __device__ void adjoint_tile(const AdjArgs& A, const TubeDev& T, int x0, AdjSmem
     }
   }
   __syncthreads();  // srcF/srcU, gM, r0 ready; the union is free for the row buffers
-  if (tid == 0) {
+  if (tid == 0 && part == 0) {
     double s = 0.0;
     for (int k = 0; k < TXA; ++k) s += sm.dl[k];
-    A.dlt[blockIdx.x] += s;
+    A.dlt[tile] += s;
   }
 
   // C. rows: transposed WENO5 flux differences, collision terms, Runge-Kutta combination
@@ -403,9 +408,10 @@ __device__ void adjoint_tile(const AdjArgs& A, const TubeDev& T, int x0, AdjSmem
   const double bt = sm.cellv[2][c], r0 = sm.r0[c];
   double* P0 = sm.v.c.P[g][0];
   int buf = 0;
-  for (int s0 = 0; s0 < Q; s0 += NG, buf ^= 1) {
+  const int r_end = (part + 1) * Q / nparts;
+  for (int s0 = part * Q / nparts; s0 < r_end; s0 += NG, buf ^= 1) {
     const int s = s0 + g;
-    const bool rv = s < Q;
+    const bool rv = s < r_end;
     const int i = rv ? s / Qxi : 0, j = rv ? s - i * Qxi : 0;
     double* fr = sm.v.c.frow[buf][g];
     double* ur = sm.v.c.urow[buf][g];
@@ -478,12 +484,14 @@ __device__ void adjoint_tile(const AdjArgs& A, const TubeDev& T, int x0, AdjSmem
 __global__ void __launch_bounds__(NT) rlb_adjoint_kernel(AdjArgs A) {
   extern __shared__ __align__(16) unsigned char adj_smem_raw[];
   AdjSmem& sm = *reinterpret_cast<AdjSmem*>(adj_smem_raw);
-  const int2 tl = A.tiles[blockIdx.x];
+  const int K = A.split > 1 ? A.split : 1;
+  const int t = blockIdx.x / K, part = blockIdx.x - t * K;
+  const int2 tl = A.tiles[t];
   const TubeDev T = A.tubes[tl.x];
   if (T.Np == 2 && T.Nv == 5)
-    adjoint_tile<2, 5>(A, T, tl.y, sm);
+    adjoint_tile<2, 5>(A, T, t, tl.y, part, K, sm);
   else
-    adjoint_tile<NP_MAX, NV_MAX>(A, T, tl.y, sm);
+    adjoint_tile<NP_MAX, NV_MAX>(A, T, t, tl.y, part, K, sm);
 }
 
 // Seed of the state from the adjoint of the five moments of each cell: dL/dF_s = sum_a c_a(s) dL/dM_a.

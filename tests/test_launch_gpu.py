@@ -1,4 +1,4 @@
-"""Launch shapes (persistent schedules, CUDA-graph replay, tile order) and the autotuner.
+"""Launch shapes (persistent schedules, CUDA-graph replay, tile order, work items per tile) and the autotuner.
 
 Scheduling never changes the arithmetic: every shape must reproduce the default launch bit for bit, for the
 FP64 and the FP32 kernels, on a batch of uneven tubes (different Nx, Qxi, tau, boundary conditions)."""
@@ -21,12 +21,14 @@ def batch():
 
 
 SHAPES = [
-    dict(schedule=rb.SCHED_TILE, ctas_per_sm=0, graph_steps=0, order=rb.ORDER_INTERLEAVE),
-    dict(schedule=rb.SCHED_STRIDE, ctas_per_sm=0, graph_steps=0, order=rb.ORDER_COST),
-    dict(schedule=rb.SCHED_STRIDE, ctas_per_sm=1, graph_steps=3, order=rb.ORDER_INTERLEAVE),
-    dict(schedule=rb.SCHED_COUNTER, ctas_per_sm=0, graph_steps=0, order=rb.ORDER_COST),
-    dict(schedule=rb.SCHED_COUNTER, ctas_per_sm=2, graph_steps=4, order=rb.ORDER_COST),
-    dict(schedule=rb.SCHED_TILE, ctas_per_sm=0, graph_steps=7, order=rb.ORDER_COST),
+    dict(schedule=rb.SCHED_TILE, ctas_per_sm=0, graph_steps=0, order=rb.ORDER_INTERLEAVE, split=0),
+    dict(schedule=rb.SCHED_TILE, ctas_per_sm=0, graph_steps=0, order=rb.ORDER_COST, split=1),
+    dict(schedule=rb.SCHED_TILE, ctas_per_sm=0, graph_steps=0, order=rb.ORDER_COST, split=3),
+    dict(schedule=rb.SCHED_STRIDE, ctas_per_sm=0, graph_steps=0, order=rb.ORDER_COST, split=0),
+    dict(schedule=rb.SCHED_STRIDE, ctas_per_sm=1, graph_steps=3, order=rb.ORDER_INTERLEAVE, split=8),
+    dict(schedule=rb.SCHED_COUNTER, ctas_per_sm=0, graph_steps=0, order=rb.ORDER_COST, split=1),
+    dict(schedule=rb.SCHED_COUNTER, ctas_per_sm=2, graph_steps=4, order=rb.ORDER_COST, split=5),
+    dict(schedule=rb.SCHED_TILE, ctas_per_sm=0, graph_steps=7, order=rb.ORDER_COST, split=0),
 ]
 
 
@@ -65,7 +67,9 @@ def test_bad_launch_shapes_rejected():
         for bad in (dict(schedule=3, ctas_per_sm=0, graph_steps=0, order=0),
                     dict(schedule=0, ctas_per_sm=-1, graph_steps=0, order=0),
                     dict(schedule=0, ctas_per_sm=0, graph_steps=65, order=0),
-                    dict(schedule=0, ctas_per_sm=0, graph_steps=0, order=2)):
+                    dict(schedule=0, ctas_per_sm=0, graph_steps=0, order=2),
+                    dict(schedule=0, ctas_per_sm=0, graph_steps=0, order=0, split=9),
+                    dict(schedule=0, ctas_per_sm=0, graph_steps=0, order=0, split=-1)):
             with pytest.raises(rb.RlbError) as ei:
                 rb.rlb_set_launch(h, bad)
             assert ei.value.status == rb.EINVAL
