@@ -75,7 +75,7 @@ GRAD_STEPS, GRAD_EVERY, GRAD_TAU, GRAD_TAU_STAR = 1000, 50, 0.08, 0.05
 ADJ_FLOPS_PER_NODE_STAGE = 201
 
 
-def workload(name: str, nx: int | None = None):
+def workload(name: str, nx: int | None = None, ntubes: int | None = None):
     if name == "sweep":
         return W.sod_sweep(), ("Sod tube sweep: Nx=4096, tau in {1e-4,1e-3,1e-2,1e-1,1,10,inf} x Qxi in "
                                "{8,32,128,200}, Qp=3, Np=2, Nv=5, CFL 0.5 (dt=min(0.5dx,0.9tau)), open BC")
@@ -93,9 +93,10 @@ def workload(name: str, nx: int | None = None):
                                                   "Np=2, Nv=5, dt=0.5dx, open BC, tau=0.08 against the T00 profile "
                                                   "of tau*=0.05, 1000 steps, checkpoints every 50")
     if name == "gradient_batch":
-        return [W.gaussian_bumps(tau=GRAD_TAU, seed=4 + k) for k in range(64)], (
-            "64 inverse problems on Gaussian bumps (seeds 4..67): Nx=2048, Qp=3, Qxi=32, Np=2, Nv=5, dt=0.5dx, "
-            "open BC, tau=0.08 against the T00 profiles of tau*=0.05, 1000 steps, checkpoints every 50")
+        m = ntubes or 64
+        return [W.gaussian_bumps(tau=GRAD_TAU, seed=4 + k) for k in range(m)], (
+            f"{m} inverse problems on Gaussian bumps (seeds 4..{3 + m}): Nx=2048, Qp=3, Qxi=32, Np=2, Nv=5, "
+            "dt=0.5dx, open BC, tau=0.08 against the T00 profiles of tau*=0.05, 1000 steps, checkpoints every 50")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -624,7 +625,8 @@ def run_gradient(args, specs, desc, rank, world):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp64_peak,
-                     "traffic": ncu_traffic_per_launch("adjoint", args.workload), "kernel": "rlb_adjoint_kernel",
+                     "traffic": ncu_traffic_per_launch("adjoint", args.workload) if args.tubes is None else None,
+                     "kernel": "rlb_adjoint_kernel",
                      "launch_ms": adj_launch_ms,
                      "note": f"{ADJ_FLOPS_PER_NODE_STAGE} algorithmic FP64 flops per velocity node per adjoint "
                              "stage; launch time = (reverse sweep - record) / adjoint launches; peak = SMs x 2 "
@@ -656,6 +658,7 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with rlb_autotune first "
                     "(default for the batched workload)")
     ap.add_argument("--nx", type=int, default=None, help="cells of the stress tube (default 1048576)")
+    ap.add_argument("--tubes", type=int, default=None, help="tubes of the gradient_batch workload (default 64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.steps is None:
@@ -666,7 +669,7 @@ def main():
         args.precision = "f32" if args.workload == "batched" else "f64"
     if args.workload == "batched":
         args.autotune = True
-    specs, desc = workload(args.workload, args.nx)
+    specs, desc = workload(args.workload, args.nx, args.tubes)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
