@@ -134,8 +134,8 @@ struct CoefSmem {
 // m = 2..NPc+2, k = PAR, PAR+2, .. <= NVc, by the positive power series (1 - beta xi)^-m =
 // sum_r C(m+r-1, r) beta^r xi^r with int xi^r P_k tabulated. Terms of one class share one sign, so the sum
 // has no cancellation; it stops when the largest-m term drops below 1e-18 (1 - beta^2).
-template <int NPc, int NVc, int PAR>
-__device__ bool hhat_parity(double beta, double* hh_col /* [m-2][k][GW] at this cell */) {
+template <int NPc, int NVc, int PAR, int STRIDE = GW>
+__device__ bool hhat_parity(double beta, double* hh_col /* [m-2][k][STRIDE] at this cell */) {
   constexpr int NK = (NVc - PAR) / 2 + 1;
   double acc[NPc + 1][NK];
 #pragma unroll
@@ -171,7 +171,7 @@ __device__ bool hhat_parity(double beta, double* hh_col /* [m-2][k][GW] at this 
 #pragma unroll
   for (int m = 0; m <= NPc; ++m)
 #pragma unroll
-    for (int q = 0; q < NK; ++q) hh_col[((m * (NV_MAX + 1)) + PAR + 2 * q) * GW] = acc[m][q];
+    for (int q = 0; q < NK; ++q) hh_col[((m * (NV_MAX + 1)) + PAR + 2 * q) * STRIDE] = acc[m][q];
   return done;
 }
 
@@ -627,7 +627,8 @@ rlb_status ensure_series_tables(int dev) {
   for (const void* k : fp64)
     RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmem)));
   for (const void* k : rp)
-    RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmemRP)));
+    RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)rp_smem_bytes(QP_MAX * (NV_MAX + 1))));
   RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(AdjSmem)));
   RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_init_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -651,6 +652,9 @@ struct rlb_ctx {
   long long nxtot = 0;
   TubeDev* d_tubes = nullptr;
   int2* d_tiles = nullptr;
+  int2* d_wtiles = nullptr;    // reduced storage: warp tiles of RP_WT cells
+  int nwt = 0;
+  int brows = 0;               // reduced storage: coefficient rows per warp region of the stage kernel
   double* d_tab = nullptr;
   float* d_tabf = nullptr;
   void *F = nullptr, *F1 = nullptr, *F2 = nullptr;
@@ -710,6 +714,7 @@ void free_ctx(rlb_ctx* h) {
   cudaFree(h->d_dlt);
   cudaFree(h->d_tubes);
   cudaFree(h->d_tiles);
+  cudaFree(h->d_wtiles);
   cudaFree(h->d_tab);
   cudaFree(h->d_tabf);
   cudaFree(h->d_stage);
@@ -739,9 +744,10 @@ void fill_eps(double* out, int Qp, int Qxi, const double* wp, const double* wxi)
     }
 }
 
-// Tiles of TX cells of every tube: most expensive tubes first (RLB_ORDER_COST), or those tubes interleaved
-// tile by tile (RLB_ORDER_INTERLEAVE).
-std::vector<int2> build_tiles(const std::vector<rlb_tube>& tubes, int order) {
+// Tiles of `width` cells of every tube (TX for the FP64 kernels, RP_WT warp tiles for the reduced-precision
+// kernel): most expensive tubes first (RLB_ORDER_COST), or the tubes interleaved tile by tile
+// (RLB_ORDER_INTERLEAVE).
+std::vector<int2> build_tiles(const std::vector<rlb_tube>& tubes, int order, int width = TX) {
   const int ntubes = (int)tubes.size();
   std::vector<int> ord(ntubes);
   for (int b = 0; b < ntubes; ++b) ord[b] = b;
@@ -751,10 +757,10 @@ std::vector<int2> build_tiles(const std::vector<rlb_tube>& tubes, int order) {
   std::vector<int2> tiles;
   if (order == RLB_ORDER_COST) {
     for (int b : ord)
-      for (int x0 = 0; x0 < (int)tubes[b].Nx; x0 += TX) tiles.push_back(make_int2(b, x0));
+      for (int x0 = 0; x0 < (int)tubes[b].Nx; x0 += width) tiles.push_back(make_int2(b, x0));
   } else {
     bool more = true;
-    for (int x0 = 0; more; x0 += TX) {
+    for (int x0 = 0; more; x0 += width) {
       more = false;
       for (int b : ord)
         if (x0 < (int)tubes[b].Nx) {
@@ -853,24 +859,26 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
       for (int st = 0; st < 3; ++st) T[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
     }
     fill_eps(T + tab_eps(t.Qxi), t.Qp, t.Qxi, wp.data(), wxi.data());
-    // FP32 tables: hi/lo float pairs of the moment weights, and FP32 copies of the per-row factors
+    // FP32 records of the reduced-precision path, one per velocity (hi/lo float pairs of the moment weights)
     float* Tf = tabf.data() + d.tabf;
-    auto split = [](double w, float& hi, float& lo) {
-      hi = (float)w;
-      lo = (float)(w - (double)hi);
+    auto split = [](double w, float* hl) {
+      hl[0] = (float)w;
+      hl[1] = (float)(w - (double)hl[0]);
     };
-    for (int i = 0; i < t.Qp; ++i) {
-      split(pb[i], Tf[TABF_P1 + i], Tf[TABF_P1 + QP_MAX + i]);
-      split(pb[i] * pb[i], Tf[TABF_P2 + i], Tf[TABF_P2 + QP_MAX + i]);
-    }
-    for (int j = 0; j < t.Qxi; ++j) {
-      split(xi[j], Tf[TABF_X + j], Tf[TABF_X + t.Qxi + j]);
-      split(xi[j] * xi[j], Tf[TABF_X + 2 * t.Qxi + j], Tf[TABF_X + 3 * t.Qxi + j]);
-      for (int k = 0; k <= NV_MAX; ++k) Tf[tabf_pw(t.Qxi) + j * (NV_MAX + 1) + k] = (float)T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k];
-      for (int st = 0; st < 3; ++st) Tf[tabf_cxi(t.Qxi) + st * t.Qxi + j] = (float)T[tab_cxi(t.Qxi) + st * t.Qxi + j];
-    }
     for (int i = 0; i < t.Qp; ++i)
-      for (int j = 0; j < t.Qxi; ++j) Tf[tabf_iws(t.Qxi) + i * t.Qxi + j] = (float)(2.0 / (wp[i] * wxi[j]));
+      for (int j = 0; j < t.Qxi; ++j) {
+        float* r = Tf + (size_t)(i * t.Qxi + j) * RP_REC;
+        const double iws = 2.0 / (wp[i] * wxi[j]);
+        r[R_XI] = (float)xi[j];
+        for (int st = 0; st < 3; ++st) r[R_CXI + st] = (float)T[tab_cxi(t.Qxi) + st * t.Qxi + j];
+        r[R_IWS] = (float)iws;
+        r[R_C6] = (float)(6.0 * iws);
+        split(pb[i], r + R_P1);
+        split(pb[i] * pb[i], r + R_P2);
+        split(xi[j], r + R_X);
+        split(xi[j] * xi[j], r + R_X2);
+        for (int k = 0; k <= NV_MAX; ++k) r[R_PW + k] = (float)T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k];
+      }
   }
   h->state_elems = off;
   h->nxtot = xoff;
@@ -893,6 +901,11 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   RLB_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
   if (h->storage != RLB_STORAGE_F64) {
+    const std::vector<int2> wt = build_tiles(h->tubes, RLB_ORDER_COST, RP_WT);
+    h->nwt = (int)wt.size();
+    for (const rlb_tube& t : h->tubes) h->brows = std::max(h->brows, rp_brows(t.Qp, t.Np, t.Nv));
+    RLB_CUDA(cudaMalloc(&h->d_wtiles, sizeof(int2) * wt.size()));
+    RLB_CUDA(cudaMemcpy(h->d_wtiles, wt.data(), sizeof(int2) * wt.size(), cudaMemcpyHostToDevice));
     RLB_CUDA(cudaMalloc(&h->M, sizeof(double) * RLB_NFIELDS * h->nxtot));
     RLB_CUDA(cudaMalloc(&h->M1, sizeof(double) * RLB_NFIELDS * h->nxtot));
     RLB_CUDA(cudaMalloc(&h->M2, sizeof(double) * RLB_NFIELDS * h->nxtot));
@@ -911,11 +924,11 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   if (h->storage == RLB_STORAGE_F64)
     RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_kernel<1>, NT, sizeof(StageSmem)));
   else if (h->storage == RLB_STORAGE_F32)
-    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_rp_kernel<float, 1>, NT,
-                                                           sizeof(StageSmemRP)));
+    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_rp_kernel<float, 1>, RP_NT,
+                                                           rp_smem_bytes(h->brows)));
   else
-    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_rp_kernel<__nv_bfloat16, 1>, NT,
-                                                           sizeof(StageSmemRP)));
+    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_rp_kernel<__nv_bfloat16, 1>, RP_NT,
+                                                           rp_smem_bytes(h->brows)));
   if (h->occupancy < 1) h->occupancy = 1;
   // a handle whose tiles cannot fill the resident slots splits each tile's velocity rows over several CTAs
   const long long slots = (long long)h->nsm * h->occupancy;
@@ -1043,7 +1056,8 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
   void* out[3] = {h->F1, h->F2, h->F};
   const int sched = h->cfg.schedule;
   const int split = eff_split(h);
-  const int items = h->ntiles * split;
+  // work items: tiles (times the split) of the FP64 kernel, groups of RP_WARPS warp tiles otherwise
+  const int items = h->storage == RLB_STORAGE_F64 ? h->ntiles * split : (h->nwt + RP_WARPS - 1) / RP_WARPS;
   const int grid = sched == RLB_SCHED_TILE
                        ? items
                        : std::max(1, std::min(items, h->nsm * (h->cfg.ctas_per_sm > 0 ? h->cfg.ctas_per_sm
@@ -1081,7 +1095,8 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
         double* mout[3] = {h->M1, h->M2, h->M};
         StageArgsRP A{};
         A.tubes = h->d_tubes;
-        A.tiles = h->d_tiles;
+        A.wtiles = h->d_wtiles;
+        A.nwt = h->nwt;
         A.tab = h->d_tab;
         A.tabf = h->d_tabf;
         A.flag = h->d_flag;
@@ -1095,24 +1110,25 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
         A.b = (float)RK_B[st];
         A.bd = RK_B[st];
         A.stage = st;
-        A.ntiles = h->ntiles;
+        A.ngroups = items;
         A.schedule = sched;
         A.counter = ctr + st;
-        const size_t sb = sizeof(StageSmemRP);
+        A.brows = h->brows;
+        const size_t sb = rp_smem_bytes(h->brows);
         if (h->storage == RLB_STORAGE_F32) {
           if (sched == RLB_SCHED_TILE)
-            rlb_stage_rp_kernel<float, 0><<<grid, NT, sb, stream>>>(A);
+            rlb_stage_rp_kernel<float, 0><<<grid, RP_NT, sb, stream>>>(A);
           else if (sched == RLB_SCHED_STRIDE)
-            rlb_stage_rp_kernel<float, 1><<<grid, NT, sb, stream>>>(A);
+            rlb_stage_rp_kernel<float, 1><<<grid, RP_NT, sb, stream>>>(A);
           else
-            rlb_stage_rp_kernel<float, 2><<<grid, NT, sb, stream>>>(A);
+            rlb_stage_rp_kernel<float, 2><<<grid, RP_NT, sb, stream>>>(A);
         } else {
           if (sched == RLB_SCHED_TILE)
-            rlb_stage_rp_kernel<__nv_bfloat16, 0><<<grid, NT, sb, stream>>>(A);
+            rlb_stage_rp_kernel<__nv_bfloat16, 0><<<grid, RP_NT, sb, stream>>>(A);
           else if (sched == RLB_SCHED_STRIDE)
-            rlb_stage_rp_kernel<__nv_bfloat16, 1><<<grid, NT, sb, stream>>>(A);
+            rlb_stage_rp_kernel<__nv_bfloat16, 1><<<grid, RP_NT, sb, stream>>>(A);
           else
-            rlb_stage_rp_kernel<__nv_bfloat16, 2><<<grid, NT, sb, stream>>>(A);
+            rlb_stage_rp_kernel<__nv_bfloat16, 2><<<grid, RP_NT, sb, stream>>>(A);
         }
       }
     }
@@ -1182,7 +1198,12 @@ rlb_status rlb_set_launch(rlb_handle h, const rlb_launch* cfg) {
     const std::vector<int2> tiles = build_tiles(h->tubes, cfg->order);
     RLB_CUDA(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice,
                              h->stream));
-    RLB_CUDA(cudaStreamSynchronize(h->stream));  // the host vector goes out of scope
+    std::vector<int2> wt;
+    if (h->d_wtiles) {
+      wt = build_tiles(h->tubes, cfg->order, RP_WT);
+      RLB_CUDA(cudaMemcpyAsync(h->d_wtiles, wt.data(), sizeof(int2) * wt.size(), cudaMemcpyHostToDevice, h->stream));
+    }
+    RLB_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
   }
   drop_graph(h);
   h->cfg = *cfg;

@@ -74,6 +74,17 @@ __device__ __forceinline__ T weno5_combine(T s0, T s1, T s2, T d1, T d2, T d3, T
   return num * rcp_fast(T(6.0) * den);
 }
 
+// weno5_combine for differences scaled by a common factor 1/ws (indicators of the weight-normalised values):
+// c6 = 6/ws in place of 6 returns G of the unscaled values (the weights do not depend on the scale).
+template <typename T>
+__device__ __forceinline__ T weno5_combine_scaled(T s0, T s1, T s2, T d1, T d2, T d3, T d4, T c6) {
+  const T r0 = fma(T(5.0), d2, T(-2.0) * d1), r1 = fma(T(2.0), d3, d2), r2 = fma(T(4.0), d3, -d4);
+  const T a0 = s1 * s2;
+  const T num = fma(s0, fma(s2, r1, s1 * r2), a0 * r0);
+  const T den = fma(s0, s1 + s2, a0);
+  return num * rcp_fast(c6 * den);
+}
+
 // Interface value v2 + G of five samples in memory order m0..m4 around the interface between m2 and m3
 // (wind toward increasing index, fwd) or between m1 and m2 (wind toward decreasing index), computed
 // exactly as the stage kernels do: pairs first, then the combination. eps: the limiter's epsilon.

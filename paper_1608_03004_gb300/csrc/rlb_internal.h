@@ -63,19 +63,19 @@ __host__ __device__ inline int tab_pw(int Qxi) { return TAB_XI + Qxi; }
 __host__ __device__ inline int tab_cxi(int Qxi) { return TAB_XI + Qxi + Qxi * (NV_MAX + 1); }
 __host__ __device__ inline int tab_eps(int Qxi) { return tab_cxi(Qxi) + 3 * Qxi; }
 inline int tab_size(int Qp, int Qxi) { return tab_eps(Qxi) + 3 * Qp * Qxi; }
-// Per-tube FP32 tables of the reduced-precision path (floats, starting at TubeDev::tabf):
-//   [0, 2 QP_MAX)           pbar_i as a hi/lo float pair: hi at i, lo at QP_MAX + i
-//   [2 QP_MAX, 4 QP_MAX)    pbar_i^2 likewise
-//   then xi_j hi, xi_j lo, xi_j^2 hi, xi_j^2 lo (Qxi each)
-//   then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k], then b_st dt xi_j / dx at [st Qxi + j], then the WENO5
-//   epsilon terms at [3 s + 0..2] as in the FP64 table
-constexpr int TABF_P1 = 0;
-constexpr int TABF_P2 = 2 * QP_MAX;
-constexpr int TABF_X = 4 * QP_MAX;
-__host__ __device__ inline int tabf_pw(int Qxi) { return TABF_X + 4 * Qxi; }
-__host__ __device__ inline int tabf_cxi(int Qxi) { return tabf_pw(Qxi) + Qxi * (NV_MAX + 1); }
-__host__ __device__ inline int tabf_iws(int Qxi) { return tabf_cxi(Qxi) + 3 * Qxi; }
-inline int tabf_size(int Qp, int Qxi) { return tabf_iws(Qxi) + Qp * Qxi; }
+// Per-tube FP32 table of the reduced-precision path (floats, starting at TubeDev::tabf): one record of
+// RP_REC floats per velocity s = i Qxi + j, 16-byte aligned, read with vector loads:
+//   R_XI          xi_j
+//   R_CXI + st    b_st dt xi_j / dx for the three Runge-Kutta stages
+//   R_IWS         1 / ws, ws = w^p_i w^xi_j / 2 (the WENO5 limiter acts on F / ws)
+//   R_C6          6 / ws
+//   R_P1, R_P2    pbar_i and pbar_i^2 as hi/lo float pairs (moment weights)
+//   R_X, R_X2     xi_j and xi_j^2 as hi/lo float pairs
+//   R_PW + k      w^xi_j P_k(xi_j), k <= NV_MAX (zero above Nv)
+constexpr int RP_REC = 24;
+constexpr int R_XI = 0, R_CXI = 1, R_IWS = 4, R_C6 = 5, R_P1 = 6, R_P2 = 8, R_X = 10, R_X2 = 12, R_PW = 14;
+static_assert(R_PW + NV_MAX + 1 <= RP_REC, "record too small");
+inline int tabf_size(int Qp, int Qxi) { return Qp * Qxi * RP_REC; }
 
 constexpr double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};  // Shu-Osher SSP-RK3: F_out = a F^n + b (F_in + dt L(F_in))
 constexpr double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
