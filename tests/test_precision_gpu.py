@@ -103,3 +103,27 @@ def test_mixed_storage_in_one_handle_rejected():
     with pytest.raises(rb.RlbError) as ei:
         rb.rlb_init_riemann(tubes, np.array([list(a.left) + list(a.right)] * 2), np.array([-0.5, -0.5]))
     assert ei.value.status == rb.EINVAL
+
+
+@pytest.mark.parametrize("storage", [rb.STORAGE_F32, rb.STORAGE_BF16])
+def test_orders_and_grids_of_the_warp_tiles(storage):
+    """The reduced-precision kernel's paths in one handle: 128-cell warp tiles that are full, ragged (127,
+    129, 257 cells) or shorter than a tile (60, 9, 3, 2, 1 cells), open and periodic boundaries, odd Qxi (a
+    xi = 0 node), the generic orders (Np = 3, Nv = 8: 9 coefficient columns per radial node), and tubes of
+    different orders sharing the per-warp shared-memory layout."""
+    specs = [W.random_smooth(127, 8, 2e-2, seed=11, bc=W.BC_OPEN),
+             W.random_smooth(128, 5, 1e-2, seed=12),
+             W.random_smooth(129, 16, 5e-3, seed=13, bc=W.BC_OPEN),
+             W.random_smooth(257, 4, 3e-2, seed=14, Qp=4, Np=3, Nv=5),
+             W.random_smooth(60, 6, 1e-2, seed=15, Qp=4, Np=3, Nv=8, bc=W.BC_OPEN),
+             W.random_smooth(9, 7, 2e-2, seed=16),
+             W.random_smooth(3, 8, 1e-2, seed=17),
+             W.random_smooth(2, 8, 1e-2, seed=18, bc=W.BC_OPEN),
+             W.random_smooth(1, 8, 1e-2, seed=19, bc=W.BC_OPEN)]
+    nsteps = 10
+    fg, _ = run(specs, nsteps, storage)
+    for s, f in zip(specs, fg):
+        _, fr = H.oracle_run(s, nsteps)
+        err = errors(f, fr)
+        print(f"storage {storage}: Nx={s.Nx} Qp={s.Qp} Np={s.Np} Nv={s.Nv} Qxi={s.Qxi} bc={s.bc} errors {err}")
+        check_bounds(err, storage)
