@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -175,7 +176,7 @@ __device__ bool hhat_parity(double beta, double* hh_col /* [m-2][k][STRIDE] at t
   return done;
 }
 
-// Fill B[i (NV_MAX+1) + k][c] for the TX cells of a tile from cs.cell (n, T, beta) and cs.ok:
+// Fill B[i (NVc+1) + k][c] (radial rows i < Qp) for the TX cells of a tile from cs.cell (n, T, beta) and cs.ok:
 //   F^eq_ij = sum_k B[i][k] w^xi_j P_k(xi_j),  B[i][k] = n/(4T^3) w^p_i sum_q s^(q+2) K[i][q] hhat_{q+2,k},
 // s = T/gamma (Eq. (feqtrunc): Laguerre generating function for the radial projection, Legendre projection
 // of each (1 - beta xi)^-m for the angular one). Groups 0/1 run the even/odd series, then group g builds
@@ -216,9 +217,9 @@ __device__ void tile_coeffs(const double* tab, int Qp, CoefSmem& cs, double (*Bs
         sq *= s;
       }
     }
-    if (i < QP_MAX) {
+    if (i < Qp) {
 #pragma unroll
-      for (int k = 0; k <= NVc; ++k) Bs[i * (NV_MAX + 1) + k][c] = B[k];
+      for (int k = 0; k <= NVc; ++k) Bs[i * (NVc + 1) + k][c] = B[k];
     }
   }
   __syncthreads();
@@ -236,14 +237,18 @@ struct StageSmem {
     double red[NG][5][GW];
     CoefSmem coef;
   } u;
-  double B[NBC][GW];
   double rate[2][GW];
   double row[2][NG][RW + 1];  // staged velocity rows (double-buffered: written before the first barrier)
   double d1[NG][RW + 1];      // first differences by position, d1[k] = row[k] - row[k-1]
+  double q1[NG][RW + 1];      // their squares
   double sp[NG][3][GW];       // scaled indicator squares, one triple per pair of adjacent differences
   double phi[NG][GW];         // WENO correction G of each interface
   int src[RW + 1];            // source cell of each staged position (boundary condition applied)
+  double B[NBC][GW];          // equilibrium coefficients B[i (NVc + 1) + k]; last, so that a launch allocates
+                              // only the rows its tubes use (stage_smem_bytes)
 };
+// Dynamic shared memory of the FP64 stage kernel for `brows` coefficient rows.
+constexpr size_t stage_smem_bytes(int brows) { return offsetof(StageSmem, B) + (size_t)brows * GW * sizeof(double); }
 
 template <int NPc, int NVc>
 __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int part, int nparts, StageSmem& sm) {
@@ -308,75 +313,100 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
   }
   __syncthreads();  // sm.src (and, with collisions, the coefficients) are ready
 
-  // C. advection + collision + Runge-Kutta combination, NG velocity rows at a time; each 64-thread group
-  //    works on its own row and synchronises with named barriers only
+  // C. advection + collision + Runge-Kutta combination. The work unit of a 64-thread group is a mirror pair
+  //    of directions (j, Qxi - 1 - j) of one radial node, processed back to back: the nodes are symmetric, so
+  //    w^xi P_k(-xi) = (-1)^k w^xi P_k(xi) and the even and odd Legendre parts of F^eq, summed once, give both
+  //    rows' equilibria (the xi = 0 node of an odd Qxi is a unit of its own). Groups synchronise with named
+  //    barriers only.
   const double a = A.a, b = A.b;
   const double* cxi_tab = tab + tab_cxi(Qxi) + A.stage * Qxi;
   double* d1 = sm.d1[g];
+  double* q1 = sm.q1[g];
   double* sp0 = sm.sp[g][0];
   double* sp1 = sm.sp[g][1];
   double* sp2 = sm.sp[g][2];
   double* phi = sm.phi[g];
+  const int hq = Qxi / 2, upr = hq + (Qxi & 1), U = Qp * upr;
+  const int u_end = (part + 1) * U / nparts;
   int buf = 0;
-  const int r_end = (part + 1) * Q / nparts;
-  for (int s0 = part * Q / nparts; s0 < r_end; s0 += NG, buf ^= 1) {
-    const int s = s0 + g;
-    const bool rv = s < r_end;
-    const int i = rv ? s / Qxi : 0, j = rv ? s - i * Qxi : 0;
-    double* row = sm.row[buf][g];
-    if (rv) {
-      const double* src = Fin + (size_t)s * ld;
-      for (int k = c; k < RW; k += GW) row[k] = __ldg(src + sm.src[k]);
-    }
-    group_sync(g);
-    const double xi = tab[TAB_XI + j];
-    const bool fwd = xi > 0.0;
-    // pairs: thread c owns the pair of differences at positions (p, p + 1), p = c + 1 (wind toward +x) or
-    // c + 2 (toward -x); these are the pairs the TX + 1 interfaces of the tile use
-    if (rv) {
-      const int p = c + (fwd ? 1 : 2);
-      const double x = row[p] - row[p - 1], y = row[p + 1] - row[p];
-      const double* et = tab + tab_eps(Qxi) + 3 * s;
-      double sa, sb, sc;
-      weno5_pair(x, y, fwd, et[0], et[1], et[2], sa, sb, sc);
-      sp0[c] = sa;
-      sp1[c] = sb;
-      sp2[c] = sc;
-      d1[p] = x;
-      if (c == GW - 1) d1[p + 1] = y;
-    }
-    group_sync(g);
-    // interfaces: interface c lies between cells x0 + c - 1 and x0 + c (row index c + 2 | c + 3); its value
-    // is v2 + G with v2 the upwind cell; D = v2(c + 1) - v2(c) is the memory-order difference d1[c + 3]
-    // (wind toward +x) or d1[c + 4] (toward -x)
-    double D = 0.0;
-    if (rv && c <= TX) {
-      double G;
-      if (fwd) {
-        D = d1[c + 3];
-        G = weno5_combine(sp0[c], sp1[c + 1], sp2[c + 2], d1[c + 1], d1[c + 2], D, d1[c + 4]);
-      } else {
-        D = d1[c + 4];
-        G = weno5_combine(sp0[c + 2], sp1[c + 1], sp2[c], -d1[c + 5], -D, -d1[c + 3], -d1[c + 2]);
+  for (int u0 = part * U / nparts; u0 < u_end; u0 += NG) {
+    const int u = u0 + g;
+    if (u >= u_end) continue;  // uniform over the group
+    const int i = u / upr, jA = u - i * upr;  // jA = hq: the xi = 0 node
+    const int nrow = jA < hq ? 2 : 1;
+    double E = 0.0, O = 0.0;  // even and odd parts of sum_k B[i][k] w^xi P_k(xi_jA) at this cell
+    for (int h = 0; h < nrow; ++h, buf ^= 1) {
+      const int j = h == 0 ? jA : Qxi - 1 - jA;
+      const int s = i * Qxi + j;
+      double* row = sm.row[buf][g];
+      // stage the row with its first differences and their squares (position k needs k - 1 as well)
+      {
+        const double* src = Fin + (size_t)s * ld;
+        for (int k = c; k < RW; k += GW) {
+          const double v = __ldg(src + sm.src[k]);
+          row[k] = v;
+          if (k > 0) {
+            const double dk = v - __ldg(src + sm.src[k - 1]);
+            d1[k] = dk;
+            q1[k] = dk * dk;
+          }
+        }
       }
-      phi[c] = G;
-    }
-    group_sync(g);
-    if (rv && cell) {
-      const double F = row[c + 3];
-      const double dphi = D + (phi[c + 1] - phi[c]);
-      double out = F;
-      if (a != 0.0) out = fma(a, Fn[(size_t)s * ld + x], b * F);
-      out = fma(-cxi_tab[j], dphi, out);  // - b dt xi/dx (Phi_{x+1/2} - Phi_{x-1/2})
-      if (T.collide) {
-        const double* pw = tab + TAB_XI + Qxi + j * (NV_MAX + 1);
-        double feq = 0.0;
+      group_sync(g);
+      const double xi = tab[TAB_XI + j];
+      const bool fwd = xi > 0.0;
+      // pairs: thread c owns the pair of differences at positions (p, p + 1), p = c + 1 (wind toward +x) or
+      // c + 2 (toward -x); these are the pairs the TX + 1 interfaces of the tile use
+      {
+        const int p = c + (fwd ? 1 : 2);
+        const double* et = tab + tab_eps(Qxi) + 3 * s;
+        double sa, sb, sc;
+        rlbdev::weno5_pair_q(q1[p], d1[p] * d1[p + 1], q1[p + 1], fwd, et[0], et[1], et[2], sa, sb, sc);
+        sp0[c] = sa;
+        sp1[c] = sb;
+        sp2[c] = sc;
+      }
+      group_sync(g);
+      // interfaces: interface c lies between cells x0 + c - 1 and x0 + c (row index c + 2 | c + 3); its value
+      // is v2 + G with v2 the upwind cell; D = v2(c + 1) - v2(c) is the memory-order difference d1[c + 3]
+      // (wind toward +x) or d1[c + 4] (toward -x)
+      double D = 0.0;
+      if (c <= TX) {
+        double G;
+        if (fwd) {
+          D = d1[c + 3];
+          G = weno5_combine(sp0[c], sp1[c + 1], sp2[c + 2], d1[c + 1], d1[c + 2], D, d1[c + 4]);
+        } else {
+          D = d1[c + 4];
+          G = weno5_combine(sp0[c + 2], sp1[c + 1], sp2[c], -d1[c + 5], -D, -d1[c + 3], -d1[c + 2]);
+        }
+        phi[c] = G;
+      }
+      group_sync(g);
+      if (cell) {
+        const double F = row[c + 3];
+        const double dphi = D + (phi[c + 1] - phi[c]);
+        double out = F;
+        if (a != 0.0) out = fma(a, Fn[(size_t)s * ld + x], b * F);
+        out = fma(-cxi_tab[j], dphi, out);  // - b dt xi/dx (Phi_{x+1/2} - Phi_{x-1/2})
+        if (T.collide) {
+          if (h == 0) {
+            const double* pw = tab + TAB_XI + Qxi + jA * (NV_MAX + 1);
 #pragma unroll
-        for (int k = 0; k <= NVc; ++k) feq = fma(sm.B[i * (NV_MAX + 1) + k][c], pw[k], feq);
-        const double rate = fma(-sm.rate[1][c], xi, sm.rate[0][c]);
-        out = fma(rate, feq - F, out);  // + b dt gamma (1 - beta xi)/tau (F^eq - F)
+            for (int k = 0; k <= NVc; ++k) {
+              const double t = sm.B[i * (NVc + 1) + k][c];
+              if (k % 2 == 0)
+                E = fma(t, pw[k], E);
+              else
+                O = fma(t, pw[k], O);
+            }
+          }
+          const double feq = h == 0 ? E + O : E - O;
+          const double rate = fma(-sm.rate[1][c], xi, sm.rate[0][c]);
+          out = fma(rate, feq - F, out);  // + b dt gamma (1 - beta xi)/tau (F^eq - F)
+        }
+        Fout[(size_t)s * ld + x] = out;
       }
-      Fout[(size_t)s * ld + x] = out;
     }
   }
 }
@@ -453,7 +483,7 @@ __device__ void init_write(const TubeDev& T, const double* tab, const InitSmem& 
     const double* pw = tab + TAB_XI + T.Qxi + j * (NV_MAX + 1);
     double f = 0.0;
 #pragma unroll
-    for (int k = 0; k <= NVc; ++k) f = fma(sm.B[i * (NV_MAX + 1) + k][c], pw[k], f);
+    for (int k = 0; k <= NVc; ++k) f = fma(sm.B[i * (NVc + 1) + k][c], pw[k], f);
     S* dst = F + T.off + (size_t)s * T.ld + x;
     st_d<S>(dst, pass1 ? 0.5 * (ld_d<S>(dst) + f) : f);
   }
@@ -655,6 +685,7 @@ struct rlb_ctx {
   int2* d_wtiles = nullptr;    // reduced storage: warp tiles of RP_WT cells
   int nwt = 0;
   int brows = 0;               // reduced storage: coefficient rows per warp region of the stage kernel
+  size_t stage_smem = 0;       // FP64: dynamic shared memory of the stage kernel (coefficient rows in use)
   double* d_tab = nullptr;
   float* d_tabf = nullptr;
   void *F = nullptr, *F1 = nullptr, *F2 = nullptr;
@@ -921,8 +952,12 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   rlb_status st = ensure_series_tables(h->dev);
   if (st != RLB_OK) return st;
   // resident CTAs per SM of this handle's stage kernel (the persistent grids' default size)
-  if (h->storage == RLB_STORAGE_F64)
-    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_kernel<1>, NT, sizeof(StageSmem)));
+  if (h->storage == RLB_STORAGE_F64) {
+    int rows = 0;
+    for (const rlb_tube& t : h->tubes) rows = std::max(rows, rp_brows(t.Qp, t.Np, t.Nv));
+    h->stage_smem = stage_smem_bytes(rows);
+    RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_kernel<1>, NT, h->stage_smem));
+  }
   else if (h->storage == RLB_STORAGE_F32)
     RLB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy, rlb_stage_rp_kernel<float, 1>, RP_NT,
                                                            rp_smem_bytes(h->brows)));
@@ -1085,11 +1120,11 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
         A.counter = ctr + st;
         A.split = split;
         if (sched == RLB_SCHED_TILE)
-          rlb_stage_kernel<0><<<grid, NT, sizeof(StageSmem), stream>>>(A);
+          rlb_stage_kernel<0><<<grid, NT, h->stage_smem, stream>>>(A);
         else if (sched == RLB_SCHED_STRIDE)
-          rlb_stage_kernel<1><<<grid, NT, sizeof(StageSmem), stream>>>(A);
+          rlb_stage_kernel<1><<<grid, NT, h->stage_smem, stream>>>(A);
         else
-          rlb_stage_kernel<2><<<grid, NT, sizeof(StageSmem), stream>>>(A);
+          rlb_stage_kernel<2><<<grid, NT, h->stage_smem, stream>>>(A);
       } else {
         const double* min[3] = {h->M, h->M1, h->M2};
         double* mout[3] = {h->M1, h->M2, h->M};
@@ -1571,7 +1606,7 @@ rlb_status launch_stage_ptrs(rlb_ctx* h, int st, const double* Fn, const double*
   A.schedule = RLB_SCHED_TILE;
   A.counter = h->d_counters;
   A.split = eff_split(h);
-  rlb_stage_kernel<0><<<h->ntiles * A.split, NT, sizeof(StageSmem), h->stream>>>(A);
+  rlb_stage_kernel<0><<<h->ntiles * A.split, NT, h->stage_smem, h->stream>>>(A);
   return cuda_status(cudaGetLastError());
 }
 

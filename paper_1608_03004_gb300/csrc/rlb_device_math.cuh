@@ -63,6 +63,20 @@ __device__ __forceinline__ void weno5_pair(T x, T y, bool fwd, T eA, T eB, T eC,
   sC = uC * uC;
 }
 
+// weno5_pair from the products x^2, x y, y^2 (the FP64 kernel forms each difference's square once and shares
+// it between the two pairs the difference belongs to).
+template <typename T>
+__device__ __forceinline__ void weno5_pair_q(T qx, T pxy, T qy, bool fwd, T eA, T eB, T eC, T& sA, T& sB, T& sC) {
+  const T ax = fwd ? T(4.0 * C0) : T(10.0 * C0), ay = fwd ? T(10.0 * C0) : T(4.0 * C0);
+  const T cx = fwd ? T(10.0 * C2) : T(4.0 * C2), cy = fwd ? T(4.0 * C2) : T(10.0 * C2);
+  const T uA = fma(ax, qx, fma(T(-11.0 * C0), pxy, fma(ay, qy, eA)));
+  const T uB = fma(T(4.0 * C1), qx, fma(T(-5.0 * C1), pxy, fma(T(4.0 * C1), qy, eB)));
+  const T uC = fma(cx, qx, fma(T(-11.0 * C2), pxy, fma(cy, qy, eC)));
+  sA = uA * uA;
+  sB = uB * uB;
+  sC = uC * uC;
+}
+
 // G of the interface from the three scaled squares (s0, s1, s2) of its stencils and the differences
 // d1..d4 in wind order.
 template <typename T>
