@@ -254,7 +254,7 @@ template <int NPc, int NVc>
 __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int part, int nparts, StageSmem& sm) {
   const int tid = threadIdx.x, c = tid % GW, g = tid / GW;
   const double* tab = A.tab + T.tab;
-  const int Qp = T.Qp, Qxi = T.Qxi, Q = Qp * Qxi, Nx = T.Nx, ld = T.ld;
+  const int Qp = T.Qp, Qxi = T.Qxi, Nx = T.Nx, ld = T.ld;
   const double* Fin = A.Fin + T.off;
   const double* Fn = A.Fn + T.off;
   double* Fout = A.Fout + T.off;
@@ -656,9 +656,13 @@ rlb_status ensure_series_tables(int dev) {
                        (const void*)rlb_stage_rp_kernel<__nv_bfloat16, 2>};
   for (const void* k : fp64)
     RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StageSmem)));
-  for (const void* k : rp)
+  for (const void* k : rp) {
     RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)rp_smem_bytes(QP_MAX * (NV_MAX + 1))));
+    // the whole carveout as shared memory, so that shared memory never limits the CTAs per SM below the
+    // register limit
+    RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  }
   RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(AdjSmem)));
   RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_init_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1373,6 +1377,23 @@ static rlb_status copy_state(rlb_handle h, double* host_or_dev, const double* sr
     return RLB_OK;
   }
   double* F = static_cast<double*>(h->F);
+  // rows without padding (Nx a multiple of the row alignment in every tube): the handle's state is the packed
+  // layout itself, one copy
+  bool packed = true;
+  for (const TubeDev& d : h->td) packed = packed && d.ld == d.Nx;
+  if (packed) {
+    cudaMemcpyKind kind;
+    if (to_handle)
+      kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    else
+      kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (to_handle)
+      RLB_CUDA(cudaMemcpyAsync(F, src_const, sizeof(double) * h->packed, kind, h->stream));
+    else
+      RLB_CUDA(cudaMemcpyAsync(host_or_dev, F, sizeof(double) * h->packed, kind, h->stream));
+    if (!on_device || !to_handle) return check_flag(h);
+    return RLB_OK;
+  }
   long long p = 0;
   for (size_t b = 0; b < h->tubes.size(); ++b) {
     const TubeDev& d = h->td[b];

@@ -13,7 +13,8 @@
 //  - the per-velocity constants are one 24-float record (six vector loads, uniform over the warp);
 //  - the moments of a stage's input are not re-read: the stage that wrote F_in accumulated them while
 //    storing it and left 5 FP64 moments per cell (M_in); this stage does the same for F_out (M_out);
-//  - the next row's loads are in flight while a row is evaluated;
+//  - the next row's loads are in flight while a row is evaluated, and F^n is loaded at the start of a row's
+//    evaluation (it is needed only at its end);
 //  - FP64 work is per cell only (Landau frame, Legendre series, equilibrium coefficients), kept by each lane
 //    for its own cells in shared memory, where the lane also keeps its cells' five moment sums between
 //    directions (lane-private columns: no barrier).
@@ -163,17 +164,15 @@ __device__ void cell_coeffs_rp(const double* tab, int Qp, const double mom[5], d
   rt1 = (float)(r0 * beta);
 }
 
-// One velocity row as a lane holds it: its RP_C cells, the tile's halo (edge lanes only) and F^n.
+// One velocity row as a lane holds it: its RP_C cells and the tile's halo (edge lanes only).
 struct RpRow {
   float v[RP_C];
   float h[3];
-  float fn[RP_C];
 };
 
 template <typename S>
-__device__ __forceinline__ void rp_load_row(RpRow& r, const S* Fin, const S* Fn, size_t row, int xl, bool full,
-                                            const int (&csrc)[RP_C], bool edge, const int (&hsrc)[3], bool use_fn,
-                                            int Nx) {
+__device__ __forceinline__ void rp_load_row(RpRow& r, const S* Fin, size_t row, int xl, bool full,
+                                            const int (&csrc)[RP_C], bool edge, const int (&hsrc)[3]) {
   const S* src = Fin + row;
   if (full) {
     const float4 t = ld4(src + xl);
@@ -187,22 +186,6 @@ __device__ __forceinline__ void rp_load_row(RpRow& r, const S* Fin, const S* Fn,
   }
 #pragma unroll
   for (int h = 0; h < 3; ++h) r.h[h] = edge ? ld_s<S>(src + hsrc[h]) : 0.f;
-  if (use_fn) {
-    const S* fs = Fn + row;
-    if (full) {
-      const float4 t = ld4(fs + xl);
-      r.fn[0] = t.x;
-      r.fn[1] = t.y;
-      r.fn[2] = t.z;
-      r.fn[3] = t.w;
-    } else {
-#pragma unroll
-      for (int q = 0; q < RP_C; ++q) r.fn[q] = (xl + q < Nx) ? ld_s<S>(fs + xl + q) : 0.f;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < RP_C; ++q) r.fn[q] = 0.f;
-  }
 }
 
 // Radial partial sums of the current direction for a lane's cells (the five moments are in shared memory).
@@ -215,9 +198,25 @@ struct RpMom {
 template <typename S, int NVc>
 __device__ __forceinline__ void rp_row(const StageArgsRP& A, const TubeDev& T, const float4* rec, const RpWarp& w,
                                        const RpRow& r, int i, int j, int s, int lane, int xl, bool full,
-                                       const float (&rt0)[RP_C], const float (&rt1)[RP_C], S* Fout, RpMom& mo) {
+                                       const float (&rt0)[RP_C], const float (&rt1)[RP_C], const S* Fn, S* Fout,
+                                       RpMom& mo) {
   constexpr unsigned ALL = 0xffffffffu;
   const int Qxi = T.Qxi;
+  // F^n at the lane's cells, issued first so that the WENO5 arithmetic below covers its latency
+  float fn[RP_C] = {0.f, 0.f, 0.f, 0.f};
+  if (A.a != 0.f) {
+    const S* fs = Fn + (size_t)s * T.ld;
+    if (full) {
+      const float4 t = ld4(fs + xl);
+      fn[0] = t.x;
+      fn[1] = t.y;
+      fn[2] = t.z;
+      fn[3] = t.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < RP_C; ++q) fn[q] = (xl + q < T.Nx) ? ld_s<S>(fs + xl + q) : 0.f;
+    }
+  }
   // the velocity's record: xi, b dt xi/dx of this stage, 1/ws, 6/ws, moment weights, w^xi P_k(xi)
   const float4* rp = rec + (size_t)s * (RP_REC / 4);
   const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4], r5 = rp[5];
@@ -268,7 +267,7 @@ __device__ __forceinline__ void rp_row(const StageArgsRP& A, const TubeDev& T, c
     const float F = wv[3 + q];
     const float up = fwd ? F - wv[2 + q] : wv[4 + q] - F;  // v2(X = q + 1) - v2(X = q)
     const float dphi = up + (G[q + 1] - G[q]);
-    float o = A.a != 0.f ? fmaf(A.a, r.fn[q], A.b * F) : F;
+    float o = A.a != 0.f ? fmaf(A.a, fn[q], A.b * F) : F;
     o = fmaf(-cxi, dphi, o);
     out[q] = o;
   }
@@ -346,7 +345,6 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
   S* Fout = static_cast<S*>(A.Fout) + T.off;
   const int xl = x0 + RP_C * lane;            // first cell of this lane
   const bool full = x0 + RP_WT <= Nx;         // uniform over the warp
-  const bool use_fn = A.a != 0.f;
   // sources of the halo (lane 0: x0-3 .. x0-1, lane 31: x0+RP_WT .. +2) and, for a partial tile, of the lane's
   // positions: boundary condition applied, always inside [0, Nx)
   const bool edge = lane == 0 || lane == 31;
@@ -385,9 +383,9 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
   const int Q = Qp * Qxi;
   RpRow ra_, rb_;
   int ia = 0, ja = 0;  // row held in ra_
-  rp_load_row<S>(ra_, Fin, Fn, (size_t)(ia * Qxi + ja) * ld, xl, full, csrc, edge, hsrc, use_fn, Nx);
+  rp_load_row<S>(ra_, Fin, (size_t)(ia * Qxi + ja) * ld, xl, full, csrc, edge, hsrc);
   int ib = Qp > 1 ? 1 : 0, jb = Qp > 1 ? 0 : 1;  // row held in rb_
-  if (Q > 1) rp_load_row<S>(rb_, Fin, Fn, (size_t)(ib * Qxi + jb) * ld, xl, full, csrc, edge, hsrc, use_fn, Nx);
+  if (Q > 1) rp_load_row<S>(rb_, Fin, (size_t)(ib * Qxi + jb) * ld, xl, full, csrc, edge, hsrc);
   auto advance2 = [&](int& i, int& j) {  // two rows further along the walk
 #pragma unroll
     for (int u = 0; u < 2; ++u)
@@ -397,14 +395,13 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       }
   };
   for (int r = 0; r < Q; r += 2) {
-    rp_row<S, NVc>(A, T, rec, w, ra_, ia, ja, ia * Qxi + ja, lane, xl, full, rt0, rt1, Fout, mo);
+    rp_row<S, NVc>(A, T, rec, w, ra_, ia, ja, ia * Qxi + ja, lane, xl, full, rt0, rt1, Fn, Fout, mo);
     advance2(ia, ja);
-    if (r + 2 < Q) rp_load_row<S>(ra_, Fin, Fn, (size_t)(ia * Qxi + ja) * ld, xl, full, csrc, edge, hsrc, use_fn, Nx);
+    if (r + 2 < Q) rp_load_row<S>(ra_, Fin, (size_t)(ia * Qxi + ja) * ld, xl, full, csrc, edge, hsrc);
     if (r + 1 < Q) {
-      rp_row<S, NVc>(A, T, rec, w, rb_, ib, jb, ib * Qxi + jb, lane, xl, full, rt0, rt1, Fout, mo);
+      rp_row<S, NVc>(A, T, rec, w, rb_, ib, jb, ib * Qxi + jb, lane, xl, full, rt0, rt1, Fn, Fout, mo);
       advance2(ib, jb);
-      if (r + 3 < Q)
-        rp_load_row<S>(rb_, Fin, Fn, (size_t)(ib * Qxi + jb) * ld, xl, full, csrc, edge, hsrc, use_fn, Nx);
+      if (r + 3 < Q) rp_load_row<S>(rb_, Fin, (size_t)(ib * Qxi + jb) * ld, xl, full, csrc, edge, hsrc);
     }
   }
   // FP64 moments of F_out for the next stage (collision tubes only)
@@ -422,7 +419,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
 }
 
 template <typename S, int SCHED>
-__global__ void __launch_bounds__(RP_NT, 3) rlb_stage_rp_kernel(StageArgsRP A) {
+__global__ void __launch_bounds__(RP_NT, 4) rlb_stage_rp_kernel(StageArgsRP A) {
   extern __shared__ __align__(16) float stage_rp_smem[];
   const int warp = threadIdx.x / 32;
   float* base = stage_rp_smem + (size_t)warp * RP_WT * (A.brows + 10);
