@@ -64,6 +64,7 @@ KERNEL_SRCS = {"adjoint": [os.path.join(_CSRC, "rlb_adjoint.cuh")] + _SHARED,
                "bf16": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED}
 ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
 CPU_SAMPLE_NODES = 24_000_000  # bound on the velocity nodes the oracle advances per CPU sample step
+REF_BUDGET_S = 120.0  # the reference arm's whole run (warm-up and timed steps) on the host cores
 GRAD_METRIC = "G velocity-node gradient updates/s"
 GRAD_UNIT = "G gradient updates/s"
 GRAD_STEPS, GRAD_EVERY, GRAD_TAU, GRAD_TAU_STAR = 1000, 50, 0.08, 0.05
@@ -230,16 +231,16 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_sample(specs):
-    """The workload itself if small enough, else windows of at most 4096 cells cut from its tubes (each window
-    an independent tube with the same orders, grid spacing, time step and relaxation time) up to about
-    CPU_SAMPLE_NODES velocity nodes. Returns (specs, description)."""
-    if W.total_nodes(specs) <= CPU_SAMPLE_NODES:
+def cpu_sample(specs, max_nodes: int = CPU_SAMPLE_NODES, window: int = 4096):
+    """The workload itself if small enough, else windows of at most `window` cells cut from its tubes (each
+    window an independent tube with the same orders, grid spacing, time step and relaxation time) up to about
+    max_nodes velocity nodes (at least one window). Returns (specs, description)."""
+    if W.total_nodes(specs) <= max_nodes:
         return specs, f"every tube of the workload ({W.total_nodes(specs)} velocity nodes)"
     out, nodes, k = [], 0, 0
-    while nodes < CPU_SAMPLE_NODES and k < 10000:
+    while nodes < max_nodes and k < 10000:
         base = specs[k % len(specs)]
-        nx = min(base.Nx, 4096)
+        nx = min(base.Nx, window)
         win = W.TubeSpec(Nx=nx, Qxi=base.Qxi, tau=base.tau, dt=base.dt, dx=base.dx, Qp=base.Qp, Np=base.Np,
                          Nv=base.Nv, bc=base.bc, x_left=-0.5 * nx * base.dx, left=base.left, right=base.right)
         out.append(win)
@@ -378,7 +379,20 @@ def run_reference(args, specs, desc, rank):
                 "e2e": {"value": value, "unit": GRAD_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
-    specs, what = cpu_sample(specs)
+    # the oracle's speed differs a lot between hosts (its long double arithmetic is hardware on x86 and
+    # software on Arm): measure it on a small sample first, then size each step's sample so that the whole
+    # run of warm-up and timed steps fits REF_BUDGET_S
+    calib, _ = cpu_sample(specs, max_nodes=host_cores() * 100_000, window=256)
+    pool = OraclePool(calib, host_cores())
+    try:
+        pool.step()
+        rate = W.total_nodes(calib) / pool.step()
+    finally:
+        pool.close()
+    budget = int(rate * REF_BUDGET_S / (args.warmup + args.steps))
+    # small windows when the sample is short of the full one, so that it still spreads evenly over the cores
+    specs, what = cpu_sample(specs, max_nodes=min(CPU_SAMPLE_NODES, budget),
+                             window=4096 if budget >= CPU_SAMPLE_NODES else 512)
     pool = OraclePool(specs, host_cores())
     try:
         for _ in range(args.warmup):

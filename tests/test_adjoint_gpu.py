@@ -248,3 +248,27 @@ def test_gradient_workload_full_size():
         Pm[x] -= h
         fdx = (loss_t(forward([t], Pp, spec.n, spec.v, nsteps)) - loss_t(forward([t], Pm, spec.n, spec.v, nsteps))) / (2 * h)
         assert close(gP[x], fdx, float(L), rel=1e-5), (x, gP[x], fdx)
+
+
+@pytest.mark.parametrize("Qp,Np,Nv,Qxi,bc", [(4, 3, 8, 6, W.BC_OPEN), (3, 2, 5, 7, W.BC_PERIODIC),
+                                             (4, 2, 5, 5, W.BC_OPEN)])
+def test_other_orders_match_central_differences(Qp, Np, Nv, Qxi, bc):
+    """The adjoint kernel's generic instantiation (Np = 3, Nv = 8), odd Qxi (a xi = 0 node, no advection) and
+    four radial nodes: dL/dlog tau by second-order differences, a smooth direction in (P, n, v) by fourth-order
+    ones (h = 1e-5: smooth directions converge there)."""
+    Nx, nsteps = 90, 30
+    t = rb.Tube.make(Nx, Qxi, 0.03, dt=0.5 / Nx, bc=bc, Qp=Qp, Np=Np, Nv=Nv)
+    P, n, v = smooth_fields(Nx, Qp * 10 + Qxi, vmax=0.3)
+    R = np.random.default_rng(Qxi).normal(size=(5, Nx))
+    L, glt, gP, gn, gv = adjoint_grads([t], P, n, v, nsteps, 8, R)
+    h = 1e-6
+    fd = (loss_np(forward([with_tau(t, t.tau * math.exp(h))], P, n, v, nsteps), R)
+          - loss_np(forward([with_tau(t, t.tau * math.exp(-h))], P, n, v, nsteps), R)) / (2 * h)
+    print(f"Qp={Qp} Np={Np} Nv={Nv} Qxi={Qxi}: dL/dlog tau adjoint {glt[0]:.12e} difference {fd:.12e}")
+    assert close(glt[0], fd, L)
+    x = (np.arange(Nx) + 0.5) / Nx
+    dP, dn, dv = np.sin(2 * np.pi * x), np.cos(4 * np.pi * x), 0.3 * np.sin(2 * np.pi * x + 1.0)
+    fdd = fd4(lambda s: loss_np(forward([t], P + s * dP, n + s * dn, v + s * dv, nsteps), R), h=1e-5)
+    adj = float(np.dot(gP, dP) + np.dot(gn, dn) + np.dot(gv, dv))
+    print(f"  directional: adjoint {adj:.12e} difference {fdd:.12e}")
+    assert close(adj, fdd, L)
