@@ -162,7 +162,8 @@ def _num(s: str) -> bool:
 # ---------------------------------------------------------------------------------------------------------
 
 def _oracle_worker(conn, specs):
-    """Holds the oracle states of its tubes; each 'step' message advances them by one time step."""
+    """Holds the oracle states of its tubes: 'step' advances them by one time step, 'mark' keeps the current
+    states, 'step_mark' advances the kept states by one step (leaving the kept states as they were)."""
     sys.path.insert(0, ROOT)
     import oracle
 
@@ -173,13 +174,21 @@ def _oracle_worker(conn, specs):
         params.append(p)
         states.append(oracle.init_riemann(p, s.left, s.right, s.x_left))
     conn.send("ready")
+    kept = None
     while True:
         msg = conn.recv()
         if msg == "stop":
             break
+        if msg == "mark":
+            kept = [st.copy() for st in states]
+            conn.send(0.0)
+            continue
         t0 = time.perf_counter()
         for k, p in enumerate(params):
-            states[k] = oracle.step(p, states[k], 1)
+            if msg == "step_mark":
+                oracle.step(p, kept[k], 1)  # returns a new array; the kept state is not changed
+            else:
+                states[k] = oracle.step(p, states[k], 1)
         conn.send(time.perf_counter() - t0)
 
 
@@ -209,10 +218,10 @@ class OraclePool:
             assert c.recv() == "ready"
         self.nproc = nproc
 
-    def step(self) -> float:
+    def step(self, msg: str = "step") -> float:
         t0 = time.perf_counter()
         for c in self.conns:
-            c.send("step")
+            c.send(msg)
         for c in self.conns:
             c.recv()
         return time.perf_counter() - t0
@@ -233,19 +242,24 @@ def host_cores() -> int:
 
 def cpu_sample(specs, max_nodes: int = CPU_SAMPLE_NODES, window: int = 4096):
     """The workload itself if small enough, else windows of at most `window` cells cut from its tubes (each
-    window an independent tube with the same orders, grid spacing, time step and relaxation time) up to about
-    max_nodes velocity nodes (at least one window). Returns (specs, description)."""
+    window an independent tube with the same orders, grid spacing, time step and relaxation time), taken from
+    the tubes in turn while they fit in max_nodes velocity nodes (the first window always). Returns (specs,
+    description)."""
     if W.total_nodes(specs) <= max_nodes:
         return specs, f"every tube of the workload ({W.total_nodes(specs)} velocity nodes)"
-    out, nodes, k = [], 0, 0
-    while nodes < max_nodes and k < 10000:
+    out, nodes, k, misses = [], 0, 0, 0
+    while misses < len(specs) and k < 10000:
         base = specs[k % len(specs)]
+        k += 1
         nx = min(base.Nx, window)
+        if out and nodes + nx * base.Q > max_nodes:
+            misses += 1
+            continue
+        misses = 0
         win = W.TubeSpec(Nx=nx, Qxi=base.Qxi, tau=base.tau, dt=base.dt, dx=base.dx, Qp=base.Qp, Np=base.Np,
                          Nv=base.Nv, bc=base.bc, x_left=-0.5 * nx * base.dx, left=base.left, right=base.right)
         out.append(win)
         nodes += nx * base.Q
-        k += 1
     return out, (f"{len(out)} windows of {out[0].Nx} cells cut around the membrane of the workload's tubes "
                  f"({nodes} velocity nodes)")
 
@@ -379,25 +393,32 @@ def run_reference(args, specs, desc, rank):
                 "e2e": {"value": value, "unit": GRAD_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
-    # the oracle's speed differs a lot between hosts (its long double arithmetic is hardware on x86 and
-    # software on Arm): measure it on a small sample first, then size each step's sample so that the whole
-    # run of warm-up and timed steps fits REF_BUDGET_S
-    calib, _ = cpu_sample(specs, max_nodes=host_cores() * 100_000, window=256)
-    pool = OraclePool(calib, host_cores())
-    try:
-        pool.step()
-        rate = W.total_nodes(calib) / pool.step()
-    finally:
-        pool.close()
-    budget = int(rate * REF_BUDGET_S / (args.warmup + args.steps))
-    # small windows when the sample is short of the full one, so that it still spreads evenly over the cores
-    specs, what = cpu_sample(specs, max_nodes=min(CPU_SAMPLE_NODES, budget),
-                             window=4096 if budget >= CPU_SAMPLE_NODES else 512)
-    pool = OraclePool(specs, host_cores())
-    try:
+    # The oracle's cost differs a lot between hosts (its long double arithmetic is hardware on x86, software on
+    # Arm) and grows as the flow develops (its series run only in moving cells). So: W warm-up steps advance a
+    # sample from the initial condition, and each of the K timed steps is one step from that same state, which
+    # makes every timed step cost the same. The sample is shrunk (fewer windows, then shorter ones) until one
+    # such step fits the run's per-step share of REF_BUDGET_S.
+    per_step = REF_BUDGET_S / (args.warmup + args.steps)
+    target = CPU_SAMPLE_NODES if args.warmup + args.steps <= 10 else 2_000_000
+    window = 4096
+    pool = None
+    for attempt in range(6):
+        cand, what = cpu_sample(specs, max_nodes=target, window=window)
+        pool = OraclePool(cand, host_cores())
         for _ in range(args.warmup):
             pool.step()
-        times = [pool.step() for _ in range(args.steps)]
+        pool.step("mark")
+        t = pool.step("step_mark")
+        if t <= per_step or attempt == 5:
+            break
+        pool.close()
+        if len(cand) > 1:
+            target = max(1, int(W.total_nodes(cand) * per_step / t * 0.8))
+        else:
+            window = max(64, window // 4)
+    specs = cand
+    try:
+        times = [pool.step("step_mark") for _ in range(args.steps)]
     finally:
         pool.close()
     nodes = W.total_nodes(specs)
@@ -408,8 +429,9 @@ def run_reference(args, specs, desc, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": desc, "velocity_nodes_per_step": nodes},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
-                             "sample": f"each step: one time step of {what}, plain C FP64 oracle, tubes split "
-                                       f"over {pool.nproc} processes"},
+                             "sample": f"each step: one time step of {what}, from the state after the "
+                                       f"{args.warmup} warm-up steps, plain C FP64 oracle, tubes split over "
+                                       f"{pool.nproc} processes"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
