@@ -68,6 +68,7 @@ REF_BUDGET_S = 120.0  # the reference arm's whole run (warm-up and timed steps) 
 GRAD_METRIC = "G velocity-node gradient updates/s"
 GRAD_UNIT = "G gradient updates/s"
 GRAD_STEPS, GRAD_EVERY, GRAD_TAU, GRAD_TAU_STAR = 1000, 50, 0.08, 0.05
+GRAD_CPU_STEPS = 4  # steps of each oracle run in the gradient workloads' CPU samples (two runs per gradient)
 # Algorithmic FP64 flops per velocity node per adjoint stage (FMA = 2, a division counted as one flop):
 # WENO5 interface derivative 130 (candidates 16, indicator terms 18, eps + beta_k 18, alpha_k and weights 11,
 # Phi 5, kappa_k 12, their products with the indicator terms 12, the five partials 38), adjoint flux 3, slot
@@ -378,7 +379,7 @@ def run_reference(args, specs, desc, rank):
     if args.workload.startswith("gradient"):
         vals = []
         for k in range(args.warmup + args.steps):
-            val, cores, what = oracle_gradient_sample(specs, 10)
+            val, cores, what = oracle_gradient_sample(specs, GRAD_CPU_STEPS)
             if k >= args.warmup:
                 vals.append(val)
         value = statistics.mean(vals)
@@ -675,7 +676,7 @@ def run_gradient(args, specs, desc, rank, world):
         "gpu_launches": 9 * GRAD_STEPS + 3,
     }
     if rank_prints(rank) and not args.no_cpu_baseline:
-        val, cores, what = oracle_gradient_sample(specs, 10)
+        val, cores, what = oracle_gradient_sample(specs, GRAD_CPU_STEPS)
         line["cpu_baseline"] = {"value": val, "unit": GRAD_UNIT, "cores": cores, "kind": "oracle", "sample": what}
     if rank_prints(rank):
         print(json.dumps(line), flush=True)
