@@ -413,7 +413,7 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
 
 // SCHED is the launch's schedule (compile time, so that the one-CTA-per-tile kernel carries no tile loop).
 template <int SCHED>
-__global__ void __launch_bounds__(NT, 4) rlb_stage_kernel(StageArgs A) {
+__global__ void __launch_bounds__(NT, 3) rlb_stage_kernel(StageArgs A) {
   extern __shared__ __align__(16) unsigned char stage_smem_raw[];
   StageSmem& sm = *reinterpret_cast<StageSmem*>(stage_smem_raw);
   const int K = A.split > 1 ? A.split : 1;

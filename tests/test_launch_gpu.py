@@ -62,6 +62,23 @@ def test_autotune_keeps_the_state_and_the_results():
         np.testing.assert_array_equal(rb.rlb_get_state(h), tuned)
 
 
+def test_autotune_fp64_tries_the_split_and_keeps_the_results():
+    """FP64 handle with few tiles (the automatic split is above 1, so the tuner also tries split = 1): the
+    tuned shape reproduces the default launch bit for bit."""
+    specs = batch()
+    with H.gpu_init(specs, rb.STORAGE_F64) as h:
+        rb.rlb_step(h, 2)
+        before = rb.rlb_get_state(h)
+        best, ms = rb.rlb_autotune(h, 2)
+        assert ms > 0 and best.split in (0, 1)
+        np.testing.assert_array_equal(rb.rlb_get_state(h), before)
+        rb.rlb_step(h, 5)
+        tuned = rb.rlb_get_state(h)
+    with H.gpu_init(specs, rb.STORAGE_F64) as h:
+        rb.rlb_step(h, 7)
+        np.testing.assert_array_equal(rb.rlb_get_state(h), tuned)
+
+
 def test_bad_launch_shapes_rejected():
     with H.gpu_init([W.sod_tube(64, 8, 1e-3)]) as h:
         for bad in (dict(schedule=3, ctas_per_sm=0, graph_steps=0, order=0),
