@@ -8,12 +8,16 @@
 //      Boltzmann equation");
 //   B. solves the Landau-frame eigenproblem T^mu_nu u^nu = -e u^mu for e, v, n and builds the per-cell
 //      coefficients of the truncated equilibrium of Eq. (feqtrunc);
-//   C. walks the velocity rows four at a time: stages the row (tile + 3-cell halo, boundary condition
-//      folded into the load) in shared memory, evaluates the WENO5 smoothness indicators once per pair of
-//      adjacent first differences, combines three pairs into each of the 62 interface values and writes
-//      F_out = a F^n + b (F_in + dt L(F_in)), L = advection + Anderson-Witting collision (Eq. (Boltz)).
-// The step is FP64 throughout; on GB300 the FP64 pipe (about 2 DFMA per SM per clock) bounds it, so the
-// arithmetic is arranged to spend as few FP64 instructions per velocity-node update as possible.
+//   C. lets each of its four 64-thread groups walk mirror pairs of directions (xi_j, -xi_j) of one radial
+//      node: stages a row (tile + 3-cell halo, boundary condition folded into the load) in shared memory with
+//      its first differences and their squares, evaluates the WENO5 smoothness indicators once per pair of
+//      adjacent differences, combines three pairs into each of the 62 interface values and writes
+//      F_out = a F^n + b (F_in + dt L(F_in)), L = advection + Anderson-Witting collision (Eq. (Boltz)); the
+//      even and odd Legendre parts of the equilibrium serve both rows of a pair.
+// Tiles that cannot fill the GPU are split over several CTAs by velocity rows (StageArgs::split). The FP64
+// path is FP64 throughout; on GB300 the FP64 pipe (about 2 DFMA per SM per clock) bounds it, so the
+// arithmetic is arranged to spend as few FP64 instructions per velocity-node update as possible. The
+// reduced-precision kernel (rlb_stage_rp.cuh) and the adjoint (rlb_adjoint.cuh) are included below.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
