@@ -592,7 +592,7 @@ def run_gradient(args, specs, desc, rank, world):
         rb.rlb_set_state(h, F0)
         if e:
             e[0].record(stream)
-        rb.rlb_record(h, GRAD_STEPS, GRAD_EVERY)
+        rb.rlb_record(h, GRAD_STEPS, args.every)
         if e:
             e[1].record(stream)
         rb.rlb_moments(h, fields)
@@ -623,8 +623,10 @@ def run_gradient(args, specs, desc, rank, world):
     record_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
     backward_ms = sum(e[2].elapsed_time(e[3]) for e in ev)
     total_ms, record_ms, backward_ms = reduce_max_over_ranks([total_ms, record_ms, backward_ms], world)
-    # the reverse sweep recomputes the recorded forward launches, then runs 3 GRAD_STEPS adjoint launches
-    adj_launch_ms = max(backward_ms - record_ms, 1e-9) / (3 * GRAD_STEPS * args.steps)
+    # the reverse sweep recomputes the recorded forward launches (unless the record kept the stage inputs),
+    # then runs 3 GRAD_STEPS adjoint launches
+    recompute_ms = record_ms if args.every < GRAD_STEPS else 0.0  # a kept record leaves nothing to recompute
+    adj_launch_ms = max(backward_ms - recompute_ms, 1e-9) / (3 * GRAD_STEPS * args.steps)
 
     # end to end: the autograd call from host arrays (pinned H2D of P, n, v; D2H of the four gradients)
     e2e_steps = max(2, min(args.steps, 3))
@@ -633,7 +635,7 @@ def run_gradient(args, specs, desc, rank, world):
     def user_gradient():
         lt = torch.full((len(tubes),), math.log(GRAD_TAU), dtype=torch.float64, requires_grad=True)
         Pt, nt, vt = (a.to("cuda", non_blocking=True).requires_grad_() for a in (Ph, nh, vh))
-        M = adjoint.run_moments(lt, Pt, nt, vt, tubes, GRAD_STEPS, GRAD_EVERY)
+        M = adjoint.run_moments(lt, Pt, nt, vt, tubes, GRAD_STEPS, args.every)
         (0.5 * ((M[2] - target) ** 2).sum()).backward()
         return [lt.grad.numpy(), Pt.grad.cpu().numpy(), nt.grad.cpu().numpy(), vt.grad.cpu().numpy()]
 
@@ -658,12 +660,14 @@ def run_gradient(args, specs, desc, rank, world):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "velocity_nodes": nodes, "tubes": len(specs),
-                   "step": "one gradient: record 1000 steps with checkpoints, seed, reverse sweep (recompute + "
-                           "adjoint), initial-condition adjoint",
+                   "step": ("one gradient: record 1000 steps with checkpoints every %d, seed, reverse sweep (recompute + "
+                            "adjoint), initial-condition adjoint" % args.every) if args.every < GRAD_STEPS else
+                           "one gradient: record 1000 steps keeping every stage input, seed, reverse sweep (adjoint "
+                           "only), initial-condition adjoint",
                    "record_ms_per_step": record_ms / args.steps, "backward_ms_per_step": backward_ms / args.steps,
                    "adjoint_ctas_per_launch": tiles,
                    "l2": "state %.1f MB per buffer; checkpoints and the recomputed segment %.0f MB; no flush"
-                         % (8 * nodes / 1e6, 8 * nodes * (GRAD_STEPS // GRAD_EVERY + 3 * GRAD_EVERY + 1) / 1e6),
+                         % (8 * nodes / 1e6, 8 * nodes * (-(-GRAD_STEPS // args.every) + 3 * min(args.every, GRAD_STEPS) + 1) / 1e6),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp64_peak,
@@ -671,7 +675,7 @@ def run_gradient(args, specs, desc, rank, world):
                      "kernel": "rlb_adjoint_kernel",
                      "launch_ms": adj_launch_ms,
                      "note": f"{ADJ_FLOPS_PER_NODE_STAGE} algorithmic FP64 flops per velocity node per adjoint "
-                             "stage; launch time = (reverse sweep - record) / adjoint launches; peak = SMs x 2 "
+                             "stage; launch time = (reverse sweep - recompute) / adjoint launches; peak = SMs x 2 "
                              "DFMA/clk x 2 flops x max SM clock (derived)"},
         "e2e": {"value": whole_job_rate(nodes, GRAD_STEPS * e2e_steps, world, e2e_s), "unit": GRAD_UNIT,
                 "h2d_bytes_per_step": 3 * 8 * h.nx_total, "d2h_bytes_per_step": 3 * 8 * h.nx_total + 8 * len(tubes),
@@ -701,6 +705,8 @@ def main():
                     "(default for the batched workload)")
     ap.add_argument("--nx", type=int, default=None, help="cells of the stress tube (default 1048576)")
     ap.add_argument("--tubes", type=int, default=None, help="tubes of the gradient_batch workload (default 64)")
+    ap.add_argument("--every", type=int, default=GRAD_EVERY, help="checkpoint interval of the gradient workloads "
+                    "(default 50; >= 1000 keeps every stage input and recomputes nothing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.steps is None:

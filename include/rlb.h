@@ -238,7 +238,9 @@ rlb_status rlb_step_static(const rlb_tube *tube, const double *F_in, double *F_o
  * rlb_record - advance every tube by nsteps steps as rlb_step does (bit-identical results), keeping a
  *   checkpoint of the state every `every` steps (the state before steps 0, every, 2 every, ...) in device
  *   memory owned by the handle; a later rlb_backward recomputes each segment of `every` steps from its
- *   checkpoint. Replaces any earlier record. Memory: ceil(nsteps / every) states.
+ *   checkpoint. Replaces any earlier record. Memory: ceil(nsteps / every) states. With every >= nsteps the
+ *   record keeps every stage input instead (3 nsteps + 1 states, the buffer rlb_backward needs anyway) and
+ *   rlb_backward recomputes nothing.
  *   Returns RLB_EINVAL (nsteps < 1, every < 1, reduced storage), RLB_ENOMEM, RLB_ECUDA, or RLB_ENONPHYS if a
  *   cell became non-physical during the run.
  */
@@ -250,8 +252,8 @@ rlb_status rlb_record(rlb_handle h, int64_t nsteps, int32_t every);
  *   grad_state:   packed state, written with dL/dF of the state before the recorded steps; may be NULL.
  *   grad_log_tau: HOST array [ntubes], written with dL/dlog(tau) of each tube (0 for tau = infinity); may be
  *                 NULL.
- *   The handle's state is not changed. Scratch: (3 every + 1) + 4 states, allocated on first use and kept
- *   until rlb_destroy. Returns RLB_EINVAL (no record, reduced storage, seed NULL), RLB_ENOMEM, RLB_ECUDA,
+ *   The handle's state is not changed. Scratch: (3 min(every, nsteps) + 1) + 4 states, allocated on first
+ *   use and kept until rlb_destroy. Returns RLB_EINVAL (no record, reduced storage, seed NULL), RLB_ENOMEM, RLB_ECUDA,
  *   RLB_ENONPHYS (a recomputed cell was non-physical).
  */
 rlb_status rlb_backward(rlb_handle h, const double *seed, double *grad_state, double *grad_log_tau);

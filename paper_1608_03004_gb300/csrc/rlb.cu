@@ -719,6 +719,7 @@ struct rlb_ctx {
   long long ckpt_cap = 0;      // states allocated
   int64_t rec_steps = 0;
   int rec_every = 0;
+  bool rec_kept = false;       // the record kept every stage input in seg (one segment, nothing to recompute)
   double* seg = nullptr;
   long long seg_cap = 0;       // states allocated
   double* adj = nullptr;       // 4 states: adjoints of F^(n+1) / F^n, F^(1), F^(2) and the F^n accumulator
@@ -1675,6 +1676,17 @@ rlb_status ensure_adjoint_tiles(rlb_ctx* h) {
   return RLB_OK;
 }
 
+// Recompute buffer of at least `states` states (the stage inputs of a segment).
+rlb_status ensure_seg(rlb_ctx* h, long long states) {
+  if (h->seg_cap >= states) return RLB_OK;
+  cudaFree(h->seg);
+  h->seg = nullptr;
+  h->seg_cap = 0;
+  RLB_CUDA(cudaMalloc(&h->seg, sizeof(double) * h->state_elems * states));
+  h->seg_cap = states;
+  return RLB_OK;
+}
+
 // Packed <-> padded FP64 state of every tube (device to device).
 rlb_status packed_to_padded(rlb_ctx* h, const double* P, double* F) {
   for (size_t b = 0; b < h->tubes.size(); ++b) {
@@ -1702,7 +1714,29 @@ rlb_status rlb_record(rlb_handle h, int64_t nsteps, int32_t every) {
   if (!h || nsteps < 1 || every < 1 || h->storage != RLB_STORAGE_F64) return RLB_EINVAL;
   DeviceGuard gd(h->dev);
   h->rec_steps = 0;
+  h->rec_kept = false;
   const long long se = h->state_elems;
+  if (every >= nsteps) {
+    // one segment: keep every stage input as the steps run (the buffer the reverse sweep would fill anyway),
+    // so that the reverse sweep recomputes nothing
+    rlb_status st = ensure_seg(h, 3 * nsteps + 1);
+    if (st != RLB_OK) return st;
+    double* S = h->seg;
+    RLB_CUDA(cudaMemcpyAsync(S, h->F, sizeof(double) * se, cudaMemcpyDeviceToDevice, h->stream));
+    for (int64_t t = 0; t < nsteps; ++t) {
+      double* Fn = S + 3 * t * se;
+      if ((st = launch_stage_ptrs(h, 0, Fn, Fn, Fn + se)) != RLB_OK) return st;
+      if ((st = launch_stage_ptrs(h, 1, Fn, Fn + se, Fn + 2 * se)) != RLB_OK) return st;
+      if ((st = launch_stage_ptrs(h, 2, Fn, Fn + 2 * se, Fn + 3 * se)) != RLB_OK) return st;
+    }
+    RLB_CUDA(cudaMemcpyAsync(h->F, S + 3 * nsteps * se, sizeof(double) * se, cudaMemcpyDeviceToDevice, h->stream));
+    st = check_flag(h);
+    if (st != RLB_OK) return st;
+    h->rec_steps = nsteps;
+    h->rec_every = (int)nsteps;
+    h->rec_kept = true;
+    return RLB_OK;
+  }
   const long long nck = (nsteps + every - 1) / every;
   if (h->ckpt_cap < nck) {
     cudaFree(h->ckpt);
@@ -1731,12 +1765,9 @@ rlb_status rlb_backward(rlb_handle h, const double* seed, double* grad_state, do
   if (st != RLB_OK) return st;
   const long long se = h->state_elems;
   const int every = h->rec_every;
-  if (h->seg_cap < 3LL * every + 1) {
-    cudaFree(h->seg);
-    h->seg = nullptr;
-    h->seg_cap = 0;
-    RLB_CUDA(cudaMalloc(&h->seg, sizeof(double) * se * (3LL * every + 1)));
-    h->seg_cap = 3LL * every + 1;
+  if (!h->rec_kept) {
+    st = ensure_seg(h, 3 * std::min<int64_t>(every, h->rec_steps) + 1);
+    if (st != RLB_OK) return st;
   }
   if (!h->adj) RLB_CUDA(cudaMalloc(&h->adj, sizeof(double) * se * 4));
   double *L = h->adj, *L1 = L + se, *L2 = L1 + se, *LA = L2 + se;
@@ -1748,9 +1779,10 @@ rlb_status rlb_backward(rlb_handle h, const double* seed, double* grad_state, do
   for (long long k = nck - 1; k >= 0; --k) {
     const int64_t len = std::min<int64_t>(every, h->rec_steps - k * every);
     double* S = h->seg;
-    RLB_CUDA(cudaMemcpyAsync(S, h->ckpt + k * se, sizeof(double) * se, cudaMemcpyDeviceToDevice, h->stream));
-    // recompute the segment, keeping the three stage inputs of every step
-    for (int64_t t = 0; t < len; ++t) {
+    if (!h->rec_kept)
+      RLB_CUDA(cudaMemcpyAsync(S, h->ckpt + k * se, sizeof(double) * se, cudaMemcpyDeviceToDevice, h->stream));
+    // recompute the segment, keeping the three stage inputs of every step (unless the record kept them)
+    for (int64_t t = 0; !h->rec_kept && t < len; ++t) {
       double* Fn = S + 3 * t * se;
       if ((st = launch_stage_ptrs(h, 0, Fn, Fn, Fn + se)) != RLB_OK) return st;
       if ((st = launch_stage_ptrs(h, 1, Fn, Fn + se, Fn + 2 * se)) != RLB_OK) return st;
