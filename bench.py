@@ -59,7 +59,7 @@ PROFILES = {"adjoint": os.path.join(ROOT, "profiles", "rlb_adjoint_kernel_gradie
 _CSRC = os.path.join(ROOT, "paper_1608_03004_gb300", "csrc")
 _SHARED = [os.path.join(_CSRC, "rlb_device_math.cuh"), os.path.join(_CSRC, "rlb_internal.h")]
 KERNEL_SRCS = {"adjoint": [os.path.join(_CSRC, "rlb_adjoint.cuh")] + _SHARED,
-               "f64": [os.path.join(_CSRC, "rlb.cu")] + _SHARED,
+               "f64": [os.path.join(_CSRC, "rlb_stage.cuh")] + _SHARED,
                "f32": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED,
                "bf16": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED}
 ESIZE = {"f64": 8, "f32": 4, "bf16": 2}

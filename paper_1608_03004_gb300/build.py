@@ -15,8 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "librlb.so")
 SOURCES = [os.path.join(CSRC, "rlb.cu"), os.path.join(CSRC, "rlb_quadrature.cpp")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("rlb_internal.h", "rlb_device_math.cuh", "rlb_stage_rp.cuh",
-                                                  "rlb_adjoint.cuh")] + [os.path.join(ROOT, "include", "rlb.h")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("rlb_internal.h", "rlb_device_math.cuh", "rlb_stage.cuh",
+                                                  "rlb_stage_rp.cuh", "rlb_adjoint.cuh")] + [os.path.join(ROOT, "include", "rlb.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
