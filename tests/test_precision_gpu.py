@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import harness as H
+import oracle
 from paper_1608_03004_gb300 import binding as rb
 from paper_1608_03004_gb300 import workloads as W
 
@@ -127,3 +128,69 @@ def test_orders_and_grids_of_the_warp_tiles(storage):
         err = errors(f, fr)
         print(f"storage {storage}: Nx={s.Nx} Qp={s.Qp} Np={s.Np} Nv={s.Nv} Qxi={s.Qxi} bc={s.bc} errors {err}")
         check_bounds(err, storage)
+
+
+def _window_step_errors(specs, storage, before, xs_of, halo=9):
+    """One GPU step after `before` steps against one FP64 oracle step from the same (stored) state, on
+    windows of +-halo cells around the cells xs_of(index, spec) of each tube; the state stays on the device
+    and only the windows travel. Returns the worst error relative to each row's largest value."""
+    import torch
+
+    tot = sum(s.Q * s.Nx for s in specs)
+    with H.gpu_init(specs, storage) as h:
+        rb.rlb_step(h, before)
+        A = torch.empty(tot, dtype=torch.float64, device="cuda")
+        rb.rlb_get_state(h, A)
+        rb.rlb_step(h, 1)
+        B = torch.empty(tot, dtype=torch.float64, device="cuda")
+        rb.rlb_get_state(h, B)
+    worst, p = 0.0, 0
+    for k, s in enumerate(specs):
+        a = A[p:p + s.Q * s.Nx].view(s.Q, s.Nx)
+        b = B[p:p + s.Q * s.Nx].view(s.Q, s.Nx)
+        scale = b.abs().amax(dim=1).cpu().numpy()
+        for x in xs_of(k, s):
+            lo, hi = max(0, x - halo), min(s.Nx, x + halo + 1)
+            sub = W.TubeSpec(Nx=hi - lo, Qxi=s.Qxi, tau=s.tau, dt=s.dt, dx=s.dx, Qp=s.Qp, Np=s.Np, Nv=s.Nv, bc=s.bc)
+            ref = oracle.step(H.to_params(sub), np.ascontiguousarray(a[:, lo:hi].cpu().numpy()), 1)
+            got = b[:, x].cpu().numpy()
+            worst = max(worst, float(np.max(np.abs(got - ref[:, x - lo]) / scale)))
+        p += s.Q * s.Nx
+    return worst
+
+
+# one step from the same stored state: FP32 arithmetic and the storage rounding of the output
+ONE_STEP = {rb.STORAGE_F32: 2e-6, rb.STORAGE_BF16: 2.0**-7}
+
+
+@pytest.mark.parametrize("storage", [rb.STORAGE_F32, rb.STORAGE_BF16])
+def test_stress_tube_full_size_one_step(storage):
+    """The stress tube of the benchmark at full size (Nx = 2^20, Q = 384, one CTA per group of warp tiles):
+    after 20 steps, the next step at the membrane, at the waves and at random cells against the oracle."""
+    s = W.stress()
+    rng = np.random.default_rng(5)
+    mid = s.Nx // 2
+
+    def xs(k, sp):
+        return [mid - 1, mid, mid + 3, mid - 15, mid + 15, 0, sp.Nx - 1] + list(rng.integers(0, sp.Nx, 4))
+
+    err = _window_step_errors([s], storage, 20, xs)
+    print(f"storage {storage}: stress tube one-step error vs FP64 oracle {err:.3e}")
+    assert err <= ONE_STEP[storage], err
+
+
+def test_batched_tubes_full_size_one_step():
+    """The 256-tube batch of the benchmark (FP32, 203 M velocity nodes): after 20 steps, the next step of
+    every 16th tube near its membrane and at random cells against the oracle."""
+    specs = W.batched_tubes()
+    rng = np.random.default_rng(6)
+
+    def xs(k, sp):
+        if k % 16:
+            return []
+        m = sp.Nx // 2
+        return [m - 1, m, m + 5, 0, sp.Nx - 1] + list(rng.integers(0, sp.Nx, 2))
+
+    err = _window_step_errors(specs, rb.STORAGE_F32, 20, xs)
+    print(f"batched tubes one-step error vs FP64 oracle {err:.3e}")
+    assert err <= ONE_STEP[rb.STORAGE_F32], err
