@@ -400,7 +400,7 @@ static void fill_ghosts(orc_work *w, const double *G) {
 /* L(G) = -xi_j dG/dx - (gamma (1 - beta xi_j) / tau) (G - G^eq), the right-hand side of Eq. (Boltz). */
 static int rhs(orc_work *w, const double *G, double *L) {
   const orc_params *p = &w->p;
-  int Nx = p->Nx, Q = w->Q, Lx = Nx + 6;
+  int Nx = p->Nx, Lx = Nx + 6;
   fill_ghosts(w, G);
   /* advection, velocity by velocity, in conservative flux-difference form */
   for (int i = 0; i < p->Qp; ++i)
