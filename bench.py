@@ -273,10 +273,26 @@ def cpu_baseline(specs, desc: str) -> dict:
     finally:
         pool.close()
     nodes = W.total_nodes(sample)
+    # the same oracle on one core: one process advancing the first windows of the sample one after another
+    # (as many as make about an eighth of the sample's nodes per core, at least one)
+    few, per = [], max(1, nodes // (8 * pool.nproc))
+    for s in sample:
+        if few and W.total_nodes(few) + s.Nx * s.Q > per:
+            break
+        few.append(s)
+    single = OraclePool(few, 1)
+    try:
+        wall1 = single.step()
+    finally:
+        single.close()
     return {"value": nodes / wall / 1e9, "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
             "sample": f"one time step of {what} from the initial condition, plain C FP64 oracle, tubes split over "
                       f"{pool.nproc} processes",
-            "seconds": wall}
+            "seconds": wall,
+            "single_core": {"value": W.total_nodes(few) / wall1 / 1e9, "unit": UNIT, "cores": 1,
+                            "sample": f"one time step of the first {len(few)} of those windows "
+                                      f"({W.total_nodes(few)} velocity nodes) in one process",
+                            "seconds": wall1}}
 
 
 # ---------------------------------------------------------------------------------------------------------
