@@ -143,6 +143,28 @@ const char *rlb_error_string(rlb_status s);
 double rlb_suggest_dt(double dx, double tau, double cfl);
 
 /*
+ * rlb_stiffness_limit - the largest k dt for which one SSP-RK3 step of dF/dt = -(xi/dx) D F - k F, with D the
+ *   linear fifth-order upwind difference that WENO5 reduces to on smooth data, damps every Fourier mode at
+ *   the Courant number nu = |xi| dt / dx (host computation: bisection over k dt, modes sampled on 4096 phases).
+ *   About 2.513 at nu = 0, 1.977 at nu = 0.5; 0 if nu alone is unstable. The collision of Eq. (Boltz)
+ *   relaxes direction xi at k = gamma (1 - beta xi) / tau, largest at gamma (1 + |beta| max|xi|) / tau.
+ */
+double rlb_stiffness_limit(double nu);
+
+/*
+ * rlb_warnings - read and clear the handle's sticky warning bits (waits for the handle's stream). The step
+ *   goes on when a warning is raised; the results may be wrong.
+ *   RLB_WARN_STIFF: in some cell of a tube with collisions, dt gamma (1 + |v| max|xi|) / tau exceeded the
+ *     tube's rlb_stiffness_limit(max|xi| dt / dx): the relaxation of the fastest direction is outside the
+ *     stable region of the scheme (a smaller dt is needed for that velocity).
+ *   The bits are set by every stage a handle runs (rlb_step and the forward steps of rlb_record and
+ *   rlb_backward); rlb_step_static has no handle and checks nothing. Returns RLB_EINVAL for a null argument,
+ *   RLB_ECUDA if the read fails.
+ */
+enum { RLB_WARN_STIFF = 1 };
+rlb_status rlb_warnings(rlb_handle h, uint32_t *bits);
+
+/*
  * rlb_quadrature - the library's own nodes and weights (host, FP64): pbar[Qp], wp[Qp] for the generalised
  *   Gauss-Laguerre rule with weight pbar e^-pbar, xi[Qxi], wxi[Qxi] for Gauss-Legendre, both ascending
  *   (section "Discretization of the momentum space using quadrature rules").

@@ -45,6 +45,8 @@ from .binding import (  # noqa: F401
     rlb_state_size,
     rlb_step,
     rlb_step_static,
+    rlb_stiffness_limit,
     rlb_suggest_dt,
     rlb_sync,
+    rlb_warnings,
 )

@@ -113,6 +113,8 @@ def load():
             "rlb_set_launch": ([vp, ctypes.POINTER(Launch)], ctypes.c_int),
             "rlb_autotune": ([vp, ip, ctypes.POINTER(Launch), dp], ctypes.c_int),
             "rlb_record": ([vp, ctypes.c_int64, ip], ctypes.c_int),
+            "rlb_stiffness_limit": ([ctypes.c_double], ctypes.c_double),
+            "rlb_warnings": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
             "rlb_backward": ([vp, vp, vp, dp], ctypes.c_int),
             "rlb_moments_vjp": ([vp, vp, vp], ctypes.c_int),
             "rlb_init_vjp": ([vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
@@ -297,6 +299,21 @@ def rlb_error_string(status: int) -> str:
 
 def rlb_suggest_dt(dx: float, tau: float, cfl: float = 0.5) -> float:
     return float(load().rlb_suggest_dt(float(dx), float(tau), float(cfl)))
+
+
+WARN_STIFF = 1
+
+
+def rlb_stiffness_limit(nu: float) -> float:
+    """Largest k dt for which SSP-RK3 with (linear) WENO5 advection at Courant number nu damps every mode."""
+    return float(load().rlb_stiffness_limit(float(nu)))
+
+
+def rlb_warnings(h: Handle) -> int:
+    """Read and clear the handle's sticky warning bits (WARN_STIFF: the collision was too stiff for dt)."""
+    bits = ctypes.c_uint32()
+    _check(load().rlb_warnings(h.ptr, ctypes.byref(bits)), "rlb_warnings")
+    return int(bits.value)
 
 
 def rlb_quadrature(Qp: int, Qxi: int):

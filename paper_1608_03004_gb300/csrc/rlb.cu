@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstddef>
+#include <complex>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -315,8 +316,8 @@ struct rlb_ctx {
   double* d_stage = nullptr;   // packed FP64 staging for host state copies of reduced storage
   double *M = nullptr, *M1 = nullptr, *M2 = nullptr;  // reduced storage: FP64 moments of F, F1, F2
                                                        // ([RLB_NFIELDS][nxtot]; the first 5 rows are used)
-  int* d_flag = nullptr;
-  int* h_flag = nullptr;       // pinned
+  int* d_flag = nullptr;       // [0]: non-physical cell seen; [1]: warning bits (RLB_WARN_*)
+  int* h_flag = nullptr;       // pinned, 2 ints
   // launch shape, CUDA graph of graph_steps steps, work counters of the counter schedule
   rlb_launch cfg = {RLB_SCHED_TILE, 0, 0, RLB_ORDER_COST, 0};
   int occupancy = 1;           // resident CTAs per SM of the stage kernel
@@ -458,6 +459,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   // quadrature tables, one block per tube (FP64, and FP32 for reduced storage)
   std::vector<double> tab;
   std::vector<float> tabf;
+  std::map<double, double> stiff_memo;  // tubes of one batch often share xi_max dt / dx
   h->td.resize(ntubes);
   long long off = 0, xoff = 0;
   for (int b = 0; b < ntubes; ++b) {
@@ -491,6 +493,11 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     std::vector<double> pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
     if (!rlbq::gauss_laguerre1(t.Qp, pb.data(), wp.data()) || !rlbq::gauss_legendre(t.Qxi, xi.data(), wxi.data()))
       return RLB_EINVAL;
+    d.xi_max = 0.0;
+    for (int j = 0; j < t.Qxi; ++j) d.xi_max = std::max(d.xi_max, std::fabs(xi[j]));
+    const double nu = d.xi_max * t.dt / t.dx;
+    auto memo = stiff_memo.find(nu);
+    d.stiff_lim = memo != stiff_memo.end() ? memo->second : (stiff_memo[nu] = rlb_stiffness_limit(nu));
     for (int i = 0; i < t.Qp; ++i) {
       T[TAB_PBAR + i] = pb[i];
       T[TAB_PBAR2 + i] = pb[i] * pb[i];
@@ -547,8 +554,8 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaMalloc(&h->F, h->esize * h->state_elems));
   RLB_CUDA(cudaMalloc(&h->F1, h->esize * h->state_elems));
   RLB_CUDA(cudaMalloc(&h->F2, h->esize * h->state_elems));
-  RLB_CUDA(cudaMalloc(&h->d_flag, sizeof(int)));
-  RLB_CUDA(cudaMallocHost(&h->h_flag, sizeof(int)));
+  RLB_CUDA(cudaMalloc(&h->d_flag, 2 * sizeof(int)));
+  RLB_CUDA(cudaMallocHost(&h->h_flag, 2 * sizeof(int)));
   RLB_CUDA(cudaMalloc(&h->d_counters, sizeof(int) * 3 * GRAPH_MAX));
   RLB_CUDA(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
   RLB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -571,7 +578,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaMemsetAsync(h->F, 0, h->esize * h->state_elems, h->stream));
   RLB_CUDA(cudaMemsetAsync(h->F1, 0, h->esize * h->state_elems, h->stream));
   RLB_CUDA(cudaMemsetAsync(h->F2, 0, h->esize * h->state_elems, h->stream));
-  RLB_CUDA(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+  RLB_CUDA(cudaMemsetAsync(h->d_flag, 0, 2 * sizeof(int), h->stream));
   rlb_status st = ensure_series_tables(h->dev);
   if (st != RLB_OK) return st;
   // resident CTAs per SM of this handle's stage kernel (the persistent grids' default size)
@@ -732,6 +739,7 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
         A.tiles = h->d_tiles;
         A.tab = h->d_tab;
         A.flag = h->d_flag;
+        A.warn = h->d_flag + 1;
         A.Fn = static_cast<const double*>(h->F);
         A.Fin = static_cast<const double*>(in[st]);
         A.Fout = static_cast<double*>(out[st]);
@@ -757,7 +765,7 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
         A.nwt = h->nwt;
         A.tab = h->d_tab;
         A.tabf = h->d_tabf;
-        A.flag = h->d_flag;
+        A.flag = h->d_flag;  // two words: non-physical flag, warning bits
         A.Fn = h->F;
         A.nxtot = h->nxtot;
         A.Fin = in[st];
@@ -1079,6 +1087,51 @@ double rlb_suggest_dt(double dx, double tau, double cfl) {
   return dt;
 }
 
+double rlb_stiffness_limit(double nu) {
+  // Fourier symbol of the linear fifth-order upwind interface value (the smooth limit of WENO5),
+  // phi(th) = (2 e^-2i th - 13 e^-i th + 47 + 27 e^i th - 3 e^2i th) / 60, flux difference phi (1 - e^-i th);
+  // a step multiplies a mode by R(z) = 1 + z + z^2/2 + z^3/6, z = -nu phi (1 - e^-i th) - k dt. The symbol at
+  // -th is the conjugate of the one at th and R has real coefficients, so th in [0, pi] suffices.
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return 0.0;
+  constexpr int NTH = 2048;  // 4096 phases over the circle
+  static const std::vector<std::complex<double>> psi = [] {
+    std::vector<std::complex<double>> t(NTH + 1);
+    for (int m = 0; m <= NTH; ++m) {
+      const double th = 3.141592653589793 * m / NTH;
+      auto E = [th](int k) { return std::complex<double>(std::cos(k * th), std::sin(k * th)); };
+      const std::complex<double> phi = (2.0 * E(-2) - 13.0 * E(-1) + 47.0 + 27.0 * E(1) - 3.0 * E(2)) / 60.0;
+      t[m] = phi - phi * E(-1);
+    }
+    return t;
+  }();
+  auto growth = [nu](double kdt) {
+    double worst = 0.0;
+    for (int m = 0; m <= NTH; ++m) {
+      const std::complex<double> z = -nu * psi[m] - kdt;
+      worst = std::max(worst, std::norm(1.0 + z * (1.0 + z * (0.5 + z / 6.0))));
+    }
+    return std::sqrt(worst);
+  };
+  const double tol = 1.0 + 1e-12;
+  if (growth(0.0) > tol) return 0.0;
+  double lo = 0.0, hi = 3.0;  // the real-axis bound of SSP-RK3 is about 2.513
+  for (int it = 0; it < 40; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    (growth(mid) <= tol ? lo : hi) = mid;
+  }
+  return lo;
+}
+
+rlb_status rlb_warnings(rlb_handle h, uint32_t* bits) {
+  if (!h || !bits) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  RLB_CUDA(cudaMemcpyAsync(h->h_flag + 1, h->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  RLB_CUDA(cudaStreamSynchronize(h->stream));
+  *bits = (uint32_t)h->h_flag[1];
+  if (*bits) RLB_CUDA(cudaMemsetAsync(h->d_flag + 1, 0, sizeof(int), h->stream));
+  return RLB_OK;
+}
+
 rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double* pbar, double* wp, double* xi, double* wxi) {
   if (Qp < 1 || Qp > 64 || Qxi < 1 || Qxi > QXI_MAX || !pbar || !wp || !xi || !wxi) return RLB_EINVAL;
   if (!rlbq::gauss_laguerre1(Qp, pbar, wp) || !rlbq::gauss_legendre(Qxi, xi, wxi)) return RLB_EINVAL;
@@ -1236,6 +1289,7 @@ rlb_status launch_stage_ptrs(rlb_ctx* h, int st, const double* Fn, const double*
   A.tiles = h->d_tiles;
   A.tab = h->d_tab;
   A.flag = h->d_flag;
+  A.warn = h->d_flag + 1;
   A.Fn = Fn;
   A.Fin = Fin;
   A.Fout = Fout;

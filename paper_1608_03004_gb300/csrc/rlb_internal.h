@@ -41,6 +41,8 @@ struct TubeDev {
   int tabf;     // offset of this tube's FP32 tables (reduced-precision storage)
   int storage;  // RLB_STORAGE_F64 / F32 / BF16
   long long poff;  // offset of this tube in the packed state layout (rows of Nx cells, tube after tube)
+  double xi_max;      // largest |xi_j|
+  double stiff_lim;   // rlb_stiffness_limit(xi_max dt / dx): dt gamma (1 + |beta| xi_max) / tau above it warns
 };
 
 // Layout of one tube's tables (doubles, starting at TubeDev::tab):

@@ -25,6 +25,7 @@ struct StageArgs {
   double* Fout;       // stage output
   const double* tab;
   int* flag;
+  int* warn;          // sticky warning bits (RLB_WARN_*) or NULL
   double a, b;        // Shu-Osher combination F_out = a F^n + b (F_in + dt L(F_in))
   int stage;          // 0, 1, 2: selects the b dt xi / dx table
   int ntiles;         // tiles of this launch
@@ -73,6 +74,13 @@ __device__ __forceinline__ int map_cell(int x, int Nx, int bc) {
     return x % Nx;
   }
   return x < 0 ? 0 : (x >= Nx ? Nx - 1 : x);
+}
+
+// True where the fastest relaxation of a cell moving at beta, dt gamma (1 + |beta| max|xi|) / tau, is beyond the
+// stable region of SSP-RK3 with WENO5 advection at the tube's Courant number (TubeDev::stiff_lim).
+__device__ __forceinline__ bool stiff(const TubeDev& T, double beta) {
+  const double k = T.dt * T.inv_tau * fma(fabs(beta), T.xi_max, 1.0);  // the rate without gamma = 1 / sqrt(1 - beta^2)
+  return k * k > T.stiff_lim * T.stiff_lim * (1.0 - beta * beta);      // (k gamma)^2 > stiff_lim^2, no square root
 }
 
 // Landau frame from (N0, Nx, T00, T0x, Txx): e, beta, n (Landau), T. Returns false if non-physical.
@@ -262,6 +270,7 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
       for (int f = 0; f < 5; ++f) mom[f] = (sm.u.red[0][f][c] + sm.u.red[1][f][c]) + (sm.u.red[2][f][c] + sm.u.red[3][f][c]);
       ok = landau(mom, e, beta, n, Tt);
       if (!ok) atomicOr(A.flag, 1);
+      else if (A.warn != nullptr && stiff(T, beta)) atomicOr(A.warn, RLB_WARN_STIFF);
     }
     __syncthreads();  // the moments are consumed; the union now holds the coefficient scratch
     if (g == 0 && c < GW) {

@@ -119,10 +119,12 @@ __host__ __device__ inline int rp_brows(int Qp, int Np, int Nv) { return Qp * ((
 // FP64 kernel's tile_coeffs) stored as FP32 in column `col`, and the stage's collision rate
 // b dt gamma (1 - beta xi)/tau = rt0 - rt1 xi. A non-physical cell raises the flag and gets B = 0, rate 0.
 template <int NPc, int NVc>
-__device__ void cell_coeffs_rp(const double* tab, int Qp, const double mom[5], double bdt_itau, int* flag,
-                               const RpWarp& w, int col, float& rt0, float& rt1) {
+__device__ void cell_coeffs_rp(const TubeDev* Tg, const double* tab, int Qp, const double mom[5], double bdt_itau,
+                               int* flag, const RpWarp& w, int col, float& rt0, float& rt1) {
   double e, beta, n, Tt;
   bool ok = landau(mom, e, beta, n, Tt);
+  // flag[1] holds the sticky warning bits (RLB_WARN_*); the tube record is read from global memory here
+  if (ok && flag != nullptr && stiff(*Tg, beta)) atomicOr(flag + 1, RLB_WARN_STIFF);
   double hh[(NPc + 1) * (NV_MAX + 1)];
 #pragma unroll
   for (int k = 0; k < (NPc + 1) * (NV_MAX + 1); ++k) hh[k] = 0.0;
@@ -367,8 +369,8 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
 #pragma unroll
         for (int f = 0; f < 5; ++f) mom[f] = A.Min[f * A.nxtot + T.xoff + xl + q];
       }
-      cell_coeffs_rp<NPc, NVc>(tab, Qp, mom, bdt_itau, xl + q < Nx ? A.flag : nullptr, w, RP_C * lane + q, rt0[q],
-                               rt1[q]);
+      cell_coeffs_rp<NPc, NVc>(A.tubes + T.index, tab, Qp, mom, bdt_itau, xl + q < Nx ? A.flag : nullptr,
+                               w, RP_C * lane + q, rt0[q], rt1[q]);
     }
   }
 

@@ -189,6 +189,33 @@ def test_nonphysical_state_is_reported():
         rb.rlb_sync(h)  # the flag is cleared once reported
 
 
+@pytest.mark.parametrize("storage", [rb.STORAGE_F64, rb.STORAGE_F32])
+def test_stiff_collision_warning(storage):
+    """A uniform state keeps its velocity (no gradients to advect, the collision keeps N and T^0mu), so the
+    largest relaxation rate times dt, dt gamma (1 + |v| xi_max) / tau, is known: the warning bit is set once it
+    passes the linear stability limit at Courant number xi_max dt / dx and not below it."""
+    Nx, Qxi, tau = 64, 16, 1e-3
+    dx = 1.0 / Nx
+    dt = 0.9 * tau
+    xi_max = float(np.max(np.abs(rb.rlb_quadrature(3, Qxi)[2])))
+    lim = rb.rlb_stiffness_limit(xi_max * dt / dx)
+    assert 2.4 < lim < 2.52
+
+    def speed(stiffness):  # |v| with dt gamma (1 + v xi_max) / tau = stiffness
+        from scipy.optimize import brentq
+        return brentq(lambda v: dt / tau * (1 + v * xi_max) / np.sqrt(1 - v * v) - stiffness, 0.0, 0.999)
+
+    for v, warned in ((0.0, False), (speed(0.99 * lim), False), (speed(1.01 * lim), True), (-0.9, True)):
+        s = W.TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=dt, dx=dx, bc=W.BC_PERIODIC, x_left=0.0,
+                       P=np.ones(Nx), n=np.ones(Nx), v=np.full(Nx, v))
+        with H.gpu_init([s], storage) as h:
+            assert rb.rlb_warnings(h) == 0  # nothing stepped yet
+            rb.rlb_step(h, 2)
+            rb.rlb_sync(h)  # a warning is not an error
+            assert rb.rlb_warnings(h) == (rb.WARN_STIFF if warned else 0), v
+            assert rb.rlb_warnings(h) == 0  # read and cleared
+
+
 def test_bad_initial_state_rejected():
     s = W.random_smooth(32, 8, 1e-2, seed=5)
     s.P = s.P.copy()

@@ -47,3 +47,29 @@ def test_a_125_tau_cap_is_unstable_at_sod_speeds():
     v = 0.47
     g = 1 / np.sqrt(1 - v * v)
     assert max_growth(0.495, 1.22 * g * (1 + v)) > 1.01  # dt = 1.22 tau at Nx = 4096, tau = 1e-4, |xi| = 0.99
+
+
+def _limit(nu):
+    """Largest k dt with max_growth(nu, k dt) <= 1, by bisection on the numpy symbol above."""
+    lo, hi = 0.0, 3.0
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if max_growth(nu, mid) <= 1 + 1e-12 else (lo, mid)
+    return lo
+
+
+def test_library_stiffness_limit_matches_the_linear_analysis():
+    import shutil
+
+    import pytest
+
+    from paper_1608_03004_gb300 import binding, build
+    if shutil.which("nvcc") is None and not build.os.path.exists(build.LIB):
+        pytest.skip("no nvcc and no prebuilt library")
+    build.build()
+    for nu in (0.0, 0.1, 0.25, 0.4, 0.5):
+        assert binding.rlb_stiffness_limit(nu) == pytest.approx(_limit(nu), rel=1e-6), nu
+    # the real-axis bound of SSP-RK3, 1 + z + z^2/2 + z^3/6 = -1 at z = -2.5127
+    assert binding.rlb_stiffness_limit(0.0) == pytest.approx(2.5127453266, rel=1e-9)
+    assert max_growth(1.5, 0.0) > 1 and binding.rlb_stiffness_limit(1.5) == 0.0  # advection alone is unstable
+    assert binding.rlb_stiffness_limit(-1.0) == 0.0
