@@ -19,7 +19,7 @@
  *   T^zz = sum F pbar^2 xi^2.
  * The kinetic equation, Eq. (Boltz), is linear in f with a rate that depends on xi only, so F obeys it too.
  *
- * Readings where the paper is silent or garbled (each is listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *  - Legendre weight, Eq. (polarInt): the printed 2(1-xi_j)^2 is read as 2(1-xi_j^2) (textbook form).
  *  - The expansion coefficients of Eq. (feqtrunc) are omitted in the paper; the truncation is read as the
  *    orthogonal projection of exp(pbar) f^eq onto L^(1)_l(pbar) P_k(xi), l <= Np, k <= Nv, which is what
