@@ -64,3 +64,21 @@ def test_weno5_matches_oracle(shim):
     got = run(shim, 2, v, v.shape[0])
     ref = np.array([oracle.weno5(*row[::-1]) for row in v])
     assert (np.abs(got - ref) / scale).max() < 1e-14
+
+
+def test_fp64_fma_rate_bounds_the_derived_peak():
+    """The FP64 stage kernel is bound by the FP64 pipe; its roofline takes 2 FMAs per SM per clock at the
+    maximum SM clock (2070 MHz) as the peak. A loop of independent FMA chains measures the rate: it must
+    reach most of that peak and cannot exceed it."""
+    out = os.path.join(tempfile.mkdtemp(prefix="rlb_fp64_"), "libfp64.so")
+    subprocess.run([B.nvcc(), B.ARCH, "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", out,
+                    os.path.join(HERE, "gpu_src", "fp64_rate.cu")], check=True)
+    lib = ctypes.CDLL(out)
+    lib.fp64_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    rate, nsm = ctypes.c_double(), ctypes.c_int()
+    assert lib.fp64_rate(4096, 8, ctypes.byref(rate), ctypes.byref(nsm)) == 0
+    shutil.rmtree(os.path.dirname(out), ignore_errors=True)
+    per_sm_clock = rate.value / (nsm.value * 2070e6)
+    print(f"FP64 FMA rate {rate.value * 2 / 1e12:.3f} TFLOP/s on {nsm.value} SMs = "
+          f"{per_sm_clock:.2f} FMA per SM per clock at 2070 MHz")
+    assert 1.5 <= per_sm_clock <= 2.05, per_sm_clock
