@@ -77,15 +77,21 @@ __device__ __forceinline__ void weno5_pair_q(T qx, T pxy, T qy, bool fwd, T eA, 
   sC = uC * uC;
 }
 
-// G of the interface from the three scaled squares (s0, s1, s2) of its stencils and the differences
-// d1..d4 in wind order.
+// 6 G of the interface from the three scaled squares (s0, s1, s2) of its stencils and the differences
+// d1..d4 in wind order (the FP64 stage kernel applies the 1/6 in the flux difference, where it costs nothing).
 template <typename T>
-__device__ __forceinline__ T weno5_combine(T s0, T s1, T s2, T d1, T d2, T d3, T d4) {
+__device__ __forceinline__ T weno5_combine6(T s0, T s1, T s2, T d1, T d2, T d3, T d4) {
   const T r0 = fma(T(5.0), d2, T(-2.0) * d1), r1 = fma(T(2.0), d3, d2), r2 = fma(T(4.0), d3, -d4);
   const T a0 = s1 * s2;
   const T num = fma(s0, fma(s2, r1, s1 * r2), a0 * r0);
   const T den = fma(s0, s1 + s2, a0);
-  return num * rcp_fast(T(6.0) * den);
+  return num * rcp_fast(den);
+}
+
+// G of the interface.
+template <typename T>
+__device__ __forceinline__ T weno5_combine(T s0, T s1, T s2, T d1, T d2, T d3, T d4) {
+  return weno5_combine6(s0, s1, s2, d1, d2, d3, d4) * T(1.0 / 6.0);
 }
 
 // weno5_combine for differences scaled by a common factor 1/ws (indicators of the weight-normalised values):

@@ -216,7 +216,7 @@ struct StageSmem {
   double d1[NG][RW + 1];      // first differences by position, d1[k] = row[k] - row[k-1]
   double q1[NG][RW + 1];      // their squares
   double sp[NG][3][GW];       // scaled indicator squares, one triple per pair of adjacent differences
-  double phi[NG][GW];         // WENO correction G of each interface
+  double phi[NG][GW];         // WENO correction of each interface, times 6 (weno5_combine6)
   int src[RW + 1];            // source cell of each staged position (boundary condition applied)
   double B[NBC][GW];          // equilibrium coefficients B[i (NVc + 1) + k]; last, so that a launch allocates
                               // only the rows its tubes use (stage_smem_bytes)
@@ -350,17 +350,17 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
         double G;
         if (fwd) {
           D = d1[c + 3];
-          G = weno5_combine(sp0[c], sp1[c + 1], sp2[c + 2], d1[c + 1], d1[c + 2], D, d1[c + 4]);
+          G = rlbdev::weno5_combine6(sp0[c], sp1[c + 1], sp2[c + 2], d1[c + 1], d1[c + 2], D, d1[c + 4]);
         } else {
           D = d1[c + 4];
-          G = weno5_combine(sp0[c + 2], sp1[c + 1], sp2[c], -d1[c + 5], -D, -d1[c + 3], -d1[c + 2]);
+          G = rlbdev::weno5_combine6(sp0[c + 2], sp1[c + 1], sp2[c], -d1[c + 5], -D, -d1[c + 3], -d1[c + 2]);
         }
         phi[c] = G;
       }
       group_sync(g);
       if (cell) {
         const double F = row[c + 3];
-        const double dphi = D + (phi[c + 1] - phi[c]);
+        const double dphi = fma(phi[c + 1] - phi[c], 1.0 / 6.0, D);  // phi holds 6 G
         double out = F;
         if (a != 0.0) out = fma(a, Fn[(size_t)s * ld + x], b * F);
         out = fma(-cxi_tab[j], dphi, out);  // - b dt xi/dx (Phi_{x+1/2} - Phi_{x-1/2})
