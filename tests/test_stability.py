@@ -73,3 +73,20 @@ def test_library_stiffness_limit_matches_the_linear_analysis():
     assert binding.rlb_stiffness_limit(0.0) == pytest.approx(2.5127453266, rel=1e-9)
     assert max_growth(1.5, 0.0) > 1 and binding.rlb_stiffness_limit(1.5) == 0.0  # advection alone is unstable
     assert binding.rlb_stiffness_limit(-1.0) == 0.0
+
+
+def test_library_stiffness_limit_falls_with_the_courant_number():
+    """Advection takes part of the stable region, so the room left for the collision shrinks as nu grows,
+    down to 0 past the advective limit of SSP-RK3 with WENO5 (about 1.43)."""
+    import shutil
+
+    import pytest
+
+    from paper_1608_03004_gb300 import binding, build
+    if shutil.which("nvcc") is None and not build.os.path.exists(build.LIB):
+        pytest.skip("no nvcc and no prebuilt library")
+    build.build()
+    nus = np.linspace(0.0, 1.4, 15)
+    lims = np.array([binding.rlb_stiffness_limit(nu) for nu in nus])
+    assert np.all(np.diff(lims) < 0), lims
+    assert lims[-1] > 0.0 and binding.rlb_stiffness_limit(1.45) == 0.0
