@@ -68,8 +68,9 @@ def test_weno5_matches_oracle(shim):
 
 def test_fp64_fma_rate_bounds_the_derived_peak():
     """The FP64 stage kernel is bound by the FP64 pipe; its roofline takes 2 FMAs per SM per clock at the
-    maximum SM clock (2070 MHz) as the peak. A loop of independent FMA chains measures the rate: it must
-    reach most of that peak and cannot exceed it."""
+    maximum SM clock (2070 MHz) as the peak. A loop of independent FMA chains measures the rate: it cannot
+    exceed that peak (the denominator is not an underestimate) and reaches at least half of it even on a
+    GPU held below its maximum clock."""
     out = os.path.join(tempfile.mkdtemp(prefix="rlb_fp64_"), "libfp64.so")
     subprocess.run([B.nvcc(), B.ARCH, "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", out,
                     os.path.join(HERE, "gpu_src", "fp64_rate.cu")], check=True)
@@ -81,4 +82,4 @@ def test_fp64_fma_rate_bounds_the_derived_peak():
     per_sm_clock = rate.value / (nsm.value * 2070e6)
     print(f"FP64 FMA rate {rate.value * 2 / 1e12:.3f} TFLOP/s on {nsm.value} SMs = "
           f"{per_sm_clock:.2f} FMA per SM per clock at 2070 MHz")
-    assert 1.5 <= per_sm_clock <= 2.05, per_sm_clock
+    assert 1.0 <= per_sm_clock <= 2.05, per_sm_clock
