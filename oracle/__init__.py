@@ -82,6 +82,7 @@ def _load():
             lib.orc_weno5.restype = ctypes.c_double
             lib.orc_weno5_population.argtypes = [ctypes.c_double] * 6
             lib.orc_weno5_population.restype = ctypes.c_double
+            lib.orc_weno5_indicators.argtypes = [ctypes.c_double] * 5 + [dp]
             lib.orc_rhs.argtypes = [pp, dp, dp]
             lib.orc_step.argtypes = [pp, dp, ctypes.c_long]
             lib.orc_init.argtypes = [pp, dp, dp, dp, dp]
@@ -157,6 +158,14 @@ def weno5(vm2, vm1, v0, vp1, vp2) -> float:
 def weno5_population(ws, vm2, vm1, v0, vp1, vp2) -> float:
     """WENO5 of a population whose quadrature weight factor is ws (the scheme on F / ws, scaled back)."""
     return _load().orc_weno5_population(ws, vm2, vm1, v0, vp1, vp2)
+
+
+def weno5_indicators(vm2, vm1, v0, vp1, vp2) -> np.ndarray:
+    """The smoothness indicators (beta_0, beta_1, beta_2) of the three candidate stencils, samples in wind
+    order."""
+    out = np.zeros(3)
+    _load().orc_weno5_indicators(vm2, vm1, v0, vp1, vp2, _ptr(out))
+    return out
 
 
 def params(Qp=3, Qxi=8, Np=2, Nv=5, Nx=400, dx=None, dt=None, tau=1e-3, bc=BC_OPEN) -> Params:

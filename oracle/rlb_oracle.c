@@ -304,19 +304,33 @@ int orc_feq_cell(int Qp, int Qxi, int Np, int Nv, const double *pbar, const doub
  * blowing from v_{-2} toward v_{+2}): three third-order candidates, smoothness indicators with weights 13/12
  * and 1/4, linear weights 1/10, 6/10, 3/10 and alpha_k = d_k / (eps + beta_k)^2.
  */
+
+/* Smoothness indicator beta_k of candidate stencil k (k = 0: v_{-2} v_{-1} v_0, 1: v_{-1} v_0 v_{+1},
+ * 2: v_0 v_{+1} v_{+2}): the sum over l = 1, 2 of h^(2l-1) times the integral over the cell of v0 of the
+ * squared l-th derivative of the stencil's quadratic, written out. */
+static void weno5_indicators(double vm2, double vm1, double v0, double vp1, double vp2, double b[3]) {
+  b[0] = 13.0 / 12.0 * (vm2 - 2.0 * vm1 + v0) * (vm2 - 2.0 * vm1 + v0) +
+         0.25 * (vm2 - 4.0 * vm1 + 3.0 * v0) * (vm2 - 4.0 * vm1 + 3.0 * v0);
+  b[1] = 13.0 / 12.0 * (vm1 - 2.0 * v0 + vp1) * (vm1 - 2.0 * v0 + vp1) + 0.25 * (vm1 - vp1) * (vm1 - vp1);
+  b[2] = 13.0 / 12.0 * (v0 - 2.0 * vp1 + vp2) * (v0 - 2.0 * vp1 + vp2) +
+         0.25 * (3.0 * v0 - 4.0 * vp1 + vp2) * (3.0 * v0 - 4.0 * vp1 + vp2);
+}
+
 static double weno5_eps(double eps, double vm2, double vm1, double v0, double vp1, double vp2) {
   double q0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
   double q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
   double q2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
-  double b0 = 13.0 / 12.0 * (vm2 - 2.0 * vm1 + v0) * (vm2 - 2.0 * vm1 + v0) +
-              0.25 * (vm2 - 4.0 * vm1 + 3.0 * v0) * (vm2 - 4.0 * vm1 + 3.0 * v0);
-  double b1 = 13.0 / 12.0 * (vm1 - 2.0 * v0 + vp1) * (vm1 - 2.0 * v0 + vp1) + 0.25 * (vm1 - vp1) * (vm1 - vp1);
-  double b2 = 13.0 / 12.0 * (v0 - 2.0 * vp1 + vp2) * (v0 - 2.0 * vp1 + vp2) +
-              0.25 * (3.0 * v0 - 4.0 * vp1 + vp2) * (3.0 * v0 - 4.0 * vp1 + vp2);
-  double a0 = 0.1 / ((eps + b0) * (eps + b0));
-  double a1 = 0.6 / ((eps + b1) * (eps + b1));
-  double a2 = 0.3 / ((eps + b2) * (eps + b2));
+  double b[3];
+  weno5_indicators(vm2, vm1, v0, vp1, vp2, b);
+  double a0 = 0.1 / ((eps + b[0]) * (eps + b[0]));
+  double a1 = 0.6 / ((eps + b[1]) * (eps + b[1]));
+  double a2 = 0.3 / ((eps + b[2]) * (eps + b[2]));
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+/* The three smoothness indicators alone, for tests. */
+void orc_weno5_indicators(double vm2, double vm1, double v0, double vp1, double vp2, double *out) {
+  weno5_indicators(vm2, vm1, v0, vp1, vp2, out);
 }
 
 /* The textbook scheme on O(1) data: eps = 1e-6. */
