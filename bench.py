@@ -1,13 +1,19 @@
 #!/usr/bin/env python3
-"""Benchmark of the GB300 RLB time step: G velocity-node updates/s on the relaxation-time sweep.
+"""Benchmark of the GB300 RLB time step: G velocity-node updates/s.
 
-Workload (default ``sweep``): the paper's Sod tube, (P, n, v) = (1, 1, 0) | (0.1, 0.125, 0) on [-0.5, 0.5],
-Nx = 4096, Qp = 3, tau in {1e-4, 1e-3, 1e-2, 1e-1, 1, 10, inf} x Qxi in {8, 32, 128, 200}: 28 tubes, 31.65 M
-velocity nodes, all advanced together, one handle, FP64. A step is one SSP-RK3 time step of every tube
-(three launches of the stage kernel). One velocity-node update = one velocity at one cell over one step.
+Headline workload (default ``stress``, the largest single-GPU configuration): one Sod tube, (P, n, v) =
+(1, 1, 0) | (0.1, 0.125, 0) on [-0.5, 0.5], Nx = 1,048,576, Qp = 3, Qxi = 128 (384 velocities, 402.7 M
+velocity nodes), tau = 1e-2, CFL 0.5, open boundaries, FP64. A step is one SSP-RK3 time step (three launches
+of the stage kernel). One velocity-node update = one velocity at one cell over one step.
+
+With no --workload the line also carries, under "extra", a full record (value, ms_per_step, roofline, e2e,
+clocks) of each other configuration: the stress tube in FP32 and BF16 storage (with the ratio to FP64 on the
+same tube), the 256-tube batch autotuned in FP32 and in FP64 (and their ratio), the relaxation-time sweep
+(Nx = 4096, tau in {1e-4, 1e-3, 1e-2, 1e-1, 1, 10, inf} x Qxi in {8, 32, 128, 200}, 28 tubes) in FP64, and
+one gradient of the inverse problem on Gaussian bumps.
 
     python bench.py [--steps K] [--warmup W] [--workload sweep|small|stress|batched|gradient|gradient_batch]
-                    [--precision f64|f32|bf16] [--impl ours|reference]
+                    [--precision f64|f32|bf16] [--impl ours|reference] [--no-extras]
 
 --precision f32/bf16 stores F in that type (FP32 arithmetic, compensated moments reduced in FP64, FP64 Landau
 solve); its roofline is HBM (algorithmic 8 x element size bytes per velocity node per step).
@@ -63,6 +69,7 @@ KERNEL_SRCS = {"adjoint": [os.path.join(_CSRC, "rlb_adjoint.cuh")] + _SHARED,
                "f32": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED,
                "bf16": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED}
 ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
+EXTRA_STEPS = 40  # timed steps of each extra configuration (after the headline's warm-up count)
 CPU_SAMPLE_NODES = 24_000_000  # bound on the velocity nodes the oracle advances per CPU sample step
 REF_BUDGET_S = 120.0  # the reference arm's whole run (warm-up and timed steps) on the host cores
 GRAD_METRIC = "G velocity-node gradient updates/s"
@@ -241,13 +248,16 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_sample(specs, max_nodes: int = CPU_SAMPLE_NODES, window: int = 4096):
-    """The workload itself if small enough, else windows of at most `window` cells cut from its tubes (each
-    window an independent tube with the same orders, grid spacing, time step and relaxation time), taken from
-    the tubes in turn while they fit in max_nodes velocity nodes (the first window always). Returns (specs,
-    description)."""
+def cpu_sample(specs, max_nodes: int = CPU_SAMPLE_NODES, window: int = 4096, cores: int = 1):
+    """The workload itself if small enough, else windows cut from its tubes around the membrane (each window
+    an independent tube with the same orders, grid spacing, time step and relaxation time), taken from the
+    tubes in turn while they fit in max_nodes velocity nodes (the first window always). The windows are made
+    short enough (down to 64 cells) that the budget holds at least `cores` of them, so that one process per
+    host core has work. Returns (specs, description)."""
     if W.total_nodes(specs) <= max_nodes:
         return specs, f"every tube of the workload ({W.total_nodes(specs)} velocity nodes)"
+    qmax = max(s.Q for s in specs)
+    window = max(64, min(window, max_nodes // (max(1, cores) * qmax)))
     out, nodes, k, misses = [], 0, 0, 0
     while misses < len(specs) and k < 10000:
         base = specs[k % len(specs)]
@@ -266,7 +276,7 @@ def cpu_sample(specs, max_nodes: int = CPU_SAMPLE_NODES, window: int = 4096):
 
 
 def cpu_baseline(specs, desc: str) -> dict:
-    sample, what = cpu_sample(specs)
+    sample, what = cpu_sample(specs, cores=host_cores())
     pool = OraclePool(sample, host_cores())
     try:
         wall = pool.step()
@@ -417,11 +427,11 @@ def run_reference(args, specs, desc, rank):
     # such step fits the run's per-step share of REF_BUDGET_S.
     per_step = REF_BUDGET_S / (args.warmup + args.steps)
     target = CPU_SAMPLE_NODES if args.warmup + args.steps <= 10 else 2_000_000
-    window = 4096
+    cores = host_cores()
     pool = None
     for attempt in range(6):
-        cand, what = cpu_sample(specs, max_nodes=target, window=window)
-        pool = OraclePool(cand, host_cores())
+        cand, what = cpu_sample(specs, max_nodes=target, cores=cores)
+        pool = OraclePool(cand, cores)
         for _ in range(args.warmup):
             pool.step()
         pool.step("mark")
@@ -429,10 +439,7 @@ def run_reference(args, specs, desc, rank):
         if t <= per_step or attempt == 5:
             break
         pool.close()
-        if len(cand) > 1:
-            target = max(1, int(W.total_nodes(cand) * per_step / t * 0.8))
-        else:
-            window = max(64, window // 4)
+        target = max(1, int(W.total_nodes(cand) * per_step / t * 0.8))
     specs = cand
     try:
         times = [pool.step("step_mark") for _ in range(args.steps)]
@@ -453,13 +460,16 @@ def run_reference(args, specs, desc, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, specs, desc, rank, world):
+def measure(args, specs, desc, precision, autotune, steps, warmup, rank, world, workload_name, e2e=True):
+    """Time `steps` steps of the workload in one handle (after `warmup` steps) with CUDA events on the launching
+    stream and return the record: value, ms_per_step, roofline of the stage kernel, e2e through the C ABI with
+    host buffers, clocks sampled during the timed steps."""
     import torch
 
     from paper_1608_03004_gb300 import binding as rb
 
     dev = torch.cuda.current_device()
-    storage = rb.STORAGE[args.precision]
+    storage = rb.STORAGE[precision]
     tubes = [rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, s.tau, s.bc, storage) for s in specs]
     states = np.array([list(s.left) + list(s.right) for s in specs])
     xl = np.array([s.x_left for s in specs])
@@ -472,66 +482,70 @@ def run_ours(args, specs, desc, rank, world):
 
     h = rb.rlb_init_riemann(tubes, states, xl, stream=stream.cuda_stream)
     launch = None
-    if args.autotune:
+    if autotune:
         best, _ = rb.rlb_autotune(h, 3)
         launch = best.as_dict()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         rb.rlb_step(h, 1)
     rb.rlb_sync(h)
     torch.cuda.synchronize()
     barrier()
     visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
     clocks = ClockSampler(int(visible[dev]) if dev < len(visible) and visible[dev].isdigit() else dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     torch.cuda.synchronize()
     graph = launch is not None and launch["graph_steps"] > 0
     ev[0].record(stream)
     if graph:  # the tuned shape replays captured graphs: time the whole run as one
-        rb.rlb_step(h, args.steps)
-        ev[args.steps].record(stream)
+        rb.rlb_step(h, steps)
+        ev[steps].record(stream)
     else:
-        for k in range(args.steps):
+        for k in range(steps):
             rb.rlb_step(h, 1)
             ev[k + 1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    run_ms = ev[0].elapsed_time(ev[args.steps]) if graph else sum(
-        ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
+    run_ms = ev[0].elapsed_time(ev[steps]) if graph else sum(ev[k].elapsed_time(ev[k + 1]) for k in range(steps))
     total_ms = reduce_max_over_ranks([run_ms], world)[0]
     rb.rlb_sync(h)  # raises if any cell went non-physical during the timed steps
 
     # end to end through the public API with host buffers: H2D of the state from pinned memory, one step,
     # D2H of the fields, every step
-    e2e_steps = max(3, min(args.steps, 10))
-    host_state = torch.empty(h.state_size, dtype=torch.float64, pin_memory=True).numpy()
-    host_fields = torch.empty((rb.NFIELDS, h.nx_total), dtype=torch.float64, pin_memory=True).numpy()
-    rb.rlb_get_state(h, host_state)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        rb.rlb_set_state(h, host_state)
-        rb.rlb_step(h, 1)
-        rb.rlb_moments(h, host_fields)
-    e2e_s = reduce_max_over_ranks([time.perf_counter() - t0], world)[0]
+    e2e_rec = None
+    if e2e:
+        e2e_steps = max(3, min(steps, 10))
+        host_state = torch.empty(h.state_size, dtype=torch.float64, pin_memory=True).numpy()
+        host_fields = torch.empty((rb.NFIELDS, h.nx_total), dtype=torch.float64, pin_memory=True).numpy()
+        rb.rlb_get_state(h, host_state)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            rb.rlb_set_state(h, host_state)
+            rb.rlb_step(h, 1)
+            rb.rlb_moments(h, host_fields)
+        e2e_s = reduce_max_over_ranks([time.perf_counter() - t0], world)[0]
+        e2e_rec = {"value": whole_job_rate(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
+                   "h2d_bytes_per_step": 8 * h.state_size, "d2h_bytes_per_step": 8 * rb.NFIELDS * h.nx_total,
+                   "steps": e2e_steps, "api": "rlb_set_state(host) + rlb_step(1) + rlb_moments(host)"}
     rb.rlb_destroy(h)
 
-    value = whole_job_rate(nodes, args.steps, world, total_ms * 1e-3)
-    stage_ms = total_ms / (3 * args.steps)
+    value = whole_job_rate(nodes, steps, world, total_ms * 1e-3)
+    stage_ms = total_ms / (3 * steps)
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     hbm_peak = peaks.get("hbm_gbs", 6800.0)  # fallback: the profiling recipe's figure
-    esize = ESIZE[args.precision]
+    esize = ESIZE[precision]
     bytes_per_node_step = 8 * esize  # stage inputs read once (1 + 2 + 2), outputs written once (3)
     hbm_achieved = bytes_per_node_step * nodes / 3 / (stage_ms * 1e-3) / 1e9
-    traffic = ncu_traffic_per_launch(args.precision, args.workload) if args.nx is None else None
+    traffic = ncu_traffic_per_launch(precision, workload_name) if args.nx is None else None
     hbm = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak, "frac": hbm_achieved / hbm_peak,
            "note": f"{bytes_per_node_step} algorithmic bytes per velocity node per step, of measured copy"}
-    if args.precision == "f64":
-        # FP64: 2 DFMA per SM per clock on GB300 (measured with a DFMA loop: 1.90 per SM-clock at an assumed
-        # 2070 MHz, i.e. 1.2 TFLOP/s; nominal 1.25 TFLOP/s), 4 flops per SM per clock
+    if precision == "f64":
+        # FP64: 2 DFMA per SM per clock on GB300 (measured with a DFMA loop: 1.99 per SM-clock at 2070 MHz,
+        # 1.253 TFLOP/s; nominal 1.25 TFLOP/s), 4 flops per SM per clock
         fp64_peak = props.multi_processor_count * 4 * sm_max * 1e6 / 1e12
         achieved = FLOPS_PER_NODE_STAGE * nodes / (stage_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -542,34 +556,65 @@ def run_ours(args, specs, desc, rank, world):
     else:
         roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": hbm_achieved / hbm_peak, "traffic": traffic, "kernel": "rlb_stage_rp_kernel",
-                    "launch_ms": stage_ms, "note": hbm["note"]}
+                    "launch_ms": stage_ms, "note": hbm["note"] + " (the burst copy figure of MEASURED_PEAKS)"}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32 (moments f64)",
                                                           "bf16": "bf16 storage, f32 arithmetic (moments f64)"}[
-                                                              args.precision],
+                                                              precision],
         "data": "synthetic",
         "config": {"workload": desc, "velocity_nodes_per_step": nodes, "tubes": len(specs),
-                   "precision": args.precision, "launch": launch or "one CTA per tile, plain launches",
+                   "precision": precision, "launch": launch or "one CTA per tile, plain launches",
                    "l2": "inputs larger than L2: state %d B x nodes = %.0f MB per buffer, 3 buffers; no flush"
                          % (esize, esize * nodes / 1e6),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         "hbm": hbm,
-        "e2e": {"value": whole_job_rate(nodes, e2e_steps, world, e2e_s), "unit": UNIT,
-                "h2d_bytes_per_step": 8 * h.state_size, "d2h_bytes_per_step": 8 * rb.NFIELDS * h.nx_total,
-                "steps": e2e_steps, "api": "rlb_set_state(host) + rlb_step(1) + rlb_moments(host)"},
+        "e2e": e2e_rec,
         "clocks": clk,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 3 * steps,
     }
+    return line
+
+
+def run_ours(args, specs, desc, rank, world):
+    line = measure(args, specs, desc, args.precision, args.autotune, args.steps, args.warmup, rank, world,
+                   args.workload)
+    if args.extras:
+        line["extra"] = extras(args, rank, world, line)
     if rank_prints(rank) and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(specs, desc)
     if rank_prints(rank):
         print(json.dumps(line), flush=True)
 
 
-def run_gradient(args, specs, desc, rank, world):
+def extras(args, rank, world, head):
+    """The other configurations of the benchmark, each a full record on the headline's line: the stress tube in
+    FP32 and BF16 storage, the 256-tube batch (autotuned) in FP32 and FP64, the relaxation-time sweep in FP64
+    and one gradient of the inverse problem. Ratios to the FP64 path on the same workload and GPU are added."""
+    k = max(1, min(args.steps, EXTRA_STEPS))
+    w = args.warmup
+    out = {}
+    stress_specs, stress_desc = workload("stress")
+    for prec in ("f32", "bf16"):
+        r = measure(args, stress_specs, stress_desc, prec, False, k, w, rank, world, "stress")
+        r["vs_f64_same_workload"] = r["value"] / head["value"] if args.workload == "stress" else None
+        out[f"stress_{prec}"] = r
+    bspecs, bdesc = workload("batched")
+    for prec in ("f32", "f64"):
+        out[f"batched_{prec}"] = measure(args, bspecs, bdesc, prec, True, k, w, rank, world, "batched")
+    out["batched_f32"]["vs_f64_same_workload"] = out["batched_f32"]["value"] / out["batched_f64"]["value"]
+    sspecs, sdesc = workload("sweep")
+    out["sweep_f64"] = measure(args, sspecs, sdesc, "f64", False, k, w, rank, world, "sweep")
+    gspecs, gdesc = workload("gradient")
+    gargs = argparse.Namespace(**vars(args))
+    gargs.steps, gargs.warmup, gargs.tubes, gargs.no_cpu_baseline = 3, 3, None, True
+    out["gradient_f64"] = run_gradient(gargs, gspecs, gdesc, rank, world, emit=False)
+    return out
+
+
+def run_gradient(args, specs, desc, rank, world, emit=True):
     """Gradients of the inverse problem through the adjoint: each step is one full gradient (set the initial
     state, rlb_record, the loss's seed, rlb_backward, rlb_init_vjp)."""
     import torch
@@ -700,6 +745,8 @@ def run_gradient(args, specs, desc, rank, world):
         "clocks": clk,
         "gpu_launches": 9 * GRAD_STEPS + 3,
     }
+    if not emit:
+        return line
     if rank_prints(rank) and not args.no_cpu_baseline:
         val, cores, what = oracle_gradient_sample(specs, GRAD_CPU_STEPS)
         line["cpu_baseline"] = {"value": val, "unit": GRAD_UNIT, "cores": cores, "kind": "oracle", "sample": what}
@@ -710,11 +757,11 @@ def run_gradient(args, specs, desc, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=None, help="default 200; 5 for the gradient workloads")
+    ap.add_argument("--steps", type=int, default=None, help="default 100 for the stress tube, 200 for the other step workloads, 5 for the gradient workloads")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["sweep", "small", "stress", "batched", "gradient", "gradient_batch"],
-                    default="sweep")
+                    default=None, help="default stress, with the other configurations as extras")
     ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default=None,
                     help="default f64; f32 for the batched workload (FP32 storage, FP64 moments)")
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with rlb_autotune first "
@@ -724,9 +771,13 @@ def main():
     ap.add_argument("--every", type=int, default=GRAD_EVERY, help="checkpoint interval of the gradient workloads "
                     "(default 50; >= 1000 keeps every stage input and recomputes nothing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="time the headline workload only")
     args = ap.parse_args()
+    args.extras = args.workload is None and not args.no_extras
+    if args.workload is None:
+        args.workload = "stress"
     if args.steps is None:
-        args.steps = 5 if args.workload.startswith("gradient") else 200
+        args.steps = 5 if args.workload.startswith("gradient") else (100 if args.workload == "stress" else 200)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.precision is None:

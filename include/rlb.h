@@ -32,6 +32,9 @@
  *    and in xi, so Eq. (mom_feq) recovers it exactly only with Np >= 2, Nv >= 2 and a polar rule exact to
  *    degree Nv + 2 (section "Riemann problem" gives Qp = 3 for the same reason). Qxi <= 1024, Nx >= 1
  *    (periodic: Nx >= 3), dx > 0, dt > 0.
+ *  - Speed limit: the Legendre coefficients of the equilibrium, Eq. (feqtrunc), are summed as a positive
+ *    power series in v of at most 16384 terms, which converges for |v| <= 0.9955. A cell faster than that is
+ *    treated as non-physical: rlb_init returns RLB_EINVAL, a step sets the sticky non-physical flag.
  */
 #ifndef RLB_H
 #define RLB_H
@@ -138,7 +141,10 @@ const char *rlb_error_string(rlb_status s);
  *   paper bounds its step by the CFL condition in section "Numerical results"; cfl = 0.5 gives its
  *   dt = 0.5e-4 at dx = 1e-4) and the stiffness bound of SSP-RK3 with WENO5 advection: at cfl <= 0.5 the
  *   step is stable while dt gamma (1 + |v|) / tau <= 1.977 (linear analysis), i.e. up to |v| ~ 0.63 with
- *   0.9 tau. Faster flows need a smaller dt. tau <= 0 or infinite: cfl * dx.
+ *   0.9 tau. Faster flows need a smaller dt: near |v| = 1 the bound of the linear analysis is not enough,
+ *   because the relaxation rate gamma (1 - v xi) / tau grows with the speed it relaxes (flows at |v| = 0.97
+ *   .. 0.99 stepped at dt gamma (1 + |v|) / tau = 1.8 run away within a few steps; 0.25 .. 0.5 is stable).
+ *   tau <= 0 or infinite: cfl * dx.
  */
 double rlb_suggest_dt(double dx, double tau, double cfl);
 
@@ -238,7 +244,12 @@ rlb_status rlb_autotune(rlb_handle h, int32_t trial_steps, rlb_launch *best, dou
  *   kernel launches.
  *   Every call uses the same array and leaves its contents behind: calls that overlap on the GPU (on two
  *   streams, or from two threads) race on it and must be ordered by the caller.
- *   Returns RLB_EINVAL for bad arguments or a tube over the limit, RLB_ECUDA if a CUDA call fails.
+ *   The small tables are copied into the array from host memory that exists only during the call, so a
+ *   stream that is being captured is refused with RLB_EINVAL (a captured copy would read that memory again
+ *   at every replay). Unlike the handle-based steps, this call keeps no warning word: it reports
+ *   non-physical cells through flag but raises no stiffness warning (RLB_WARN_STIFF).
+ *   Returns RLB_EINVAL for bad arguments, a tube over the limit or a capturing stream, RLB_ECUDA if a CUDA
+ *   call fails.
  */
 #define RLB_STATIC_SCRATCH_BYTES (64u << 20)
 rlb_status rlb_step_static(const rlb_tube *tube, const double *F_in, double *F_out, int64_t nsteps,

@@ -399,6 +399,36 @@ void fill_eps(double* out, int Qp, int Qxi, const double* wp, const double* wxi)
     }
 }
 
+// The FP64 tables of one tube (layout in rlb_internal.h): quadrature nodes and weights, the radial factors
+// K[i][q], w^xi_j P_k(xi_j), the per-stage b dt xi_j / dx and the WENO5 epsilon terms. pb, wp, xi, wxi receive
+// the quadrature (Qp and Qxi entries). Returns false if a quadrature rule cannot be built.
+bool fill_tube_tables(const rlb_tube& t, double* pb, double* wp, double* xi, double* wxi, double* T) {
+  if (!rlbq::gauss_laguerre1(t.Qp, pb, wp) || !rlbq::gauss_legendre(t.Qxi, xi, wxi)) return false;
+  for (int i = 0; i < t.Qp; ++i) {
+    T[TAB_PBAR + i] = pb[i];
+    T[TAB_PBAR2 + i] = pb[i] * pb[i];
+    T[TAB_WP + i] = wp[i];
+    // K[i][q] = (-1)^q sum_{l=q}^{Np} C(l, q) L^(1)_l(pbar_i)
+    for (int q = 0; q <= t.Np; ++q) {
+      long double acc = 0.0L;
+      for (int l = q; l <= t.Np; ++l) {
+        long double C = 1.0L;
+        for (int u = 1; u <= q; ++u) C = C * (l - q + u) / u;
+        acc += C * rlbq::laguerre1(l, pb[i]);
+      }
+      T[TAB_K + i * (NP_MAX + 1) + q] = (double)((q % 2) ? -acc : acc);
+    }
+  }
+  for (int j = 0; j < t.Qxi; ++j) {
+    T[TAB_XI + j] = xi[j];
+    for (int k = 0; k <= NV_MAX; ++k)
+      T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
+    for (int st = 0; st < 3; ++st) T[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
+  }
+  fill_eps(T + tab_eps(t.Qxi), t.Qp, t.Qxi, wp, wxi);
+  return true;
+}
+
 // Tiles of `width` cells of every tube (TX for the FP64 kernels, RP_WT warp tiles for the reduced-precision
 // kernel): most expensive tubes first (RLB_ORDER_COST), or the tubes interleaved tile by tile
 // (RLB_ORDER_INTERLEAVE).
@@ -491,35 +521,12 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     tabf.resize(tabf.size() + tabf_size(t.Qp, t.Qxi), 0.0f);
     double* T = tab.data() + d.tab;
     std::vector<double> pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
-    if (!rlbq::gauss_laguerre1(t.Qp, pb.data(), wp.data()) || !rlbq::gauss_legendre(t.Qxi, xi.data(), wxi.data()))
-      return RLB_EINVAL;
+    if (!fill_tube_tables(t, pb.data(), wp.data(), xi.data(), wxi.data(), T)) return RLB_EINVAL;
     d.xi_max = 0.0;
     for (int j = 0; j < t.Qxi; ++j) d.xi_max = std::max(d.xi_max, std::fabs(xi[j]));
     const double nu = d.xi_max * t.dt / t.dx;
     auto memo = stiff_memo.find(nu);
     d.stiff_lim = memo != stiff_memo.end() ? memo->second : (stiff_memo[nu] = rlb_stiffness_limit(nu));
-    for (int i = 0; i < t.Qp; ++i) {
-      T[TAB_PBAR + i] = pb[i];
-      T[TAB_PBAR2 + i] = pb[i] * pb[i];
-      T[TAB_WP + i] = wp[i];
-      // K[i][q] = (-1)^q sum_{l=q}^{Np} C(l, q) L^(1)_l(pbar_i)
-      for (int q = 0; q <= t.Np; ++q) {
-        long double acc = 0.0L;
-        for (int l = q; l <= t.Np; ++l) {
-          long double C = 1.0L;
-          for (int u = 1; u <= q; ++u) C = C * (l - q + u) / u;
-          acc += C * rlbq::laguerre1(l, pb[i]);
-        }
-        T[TAB_K + i * (NP_MAX + 1) + q] = (double)((q % 2) ? -acc : acc);
-      }
-    }
-    for (int j = 0; j < t.Qxi; ++j) {
-      T[TAB_XI + j] = xi[j];
-      for (int k = 0; k <= NV_MAX; ++k)
-        T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
-      for (int st = 0; st < 3; ++st) T[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
-    }
-    fill_eps(T + tab_eps(t.Qxi), t.Qp, t.Qxi, wp.data(), wxi.data());
     // FP32 records of the reduced-precision path, one per velocity (hi/lo float pairs of the moment weights)
     float* Tf = tabf.data() + d.tabf;
     auto split = [](double w, float* hl) {
@@ -1193,13 +1200,18 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
   if (off_f2 + stage_bytes > (size_t)RLB_STATIC_SCRATCH_BYTES) return RLB_EINVAL;
   if (nsteps == 0) return RLB_OK;
 
+  cudaStream_t s = (cudaStream_t)stream;
+  // the tables below are copied out of host memory that lives only during this call, which a captured graph
+  // would read again at every replay: refuse a stream under capture
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RLB_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return RLB_EINVAL;
   int dev = 0;
   RLB_CUDA(cudaGetDevice(&dev));
   double* base = nullptr;
   st = static_setup(dev, &base);
   if (st != RLB_OK) return st;
   char* b = reinterpret_cast<char*>(base);
-  cudaStream_t s = (cudaStream_t)stream;
 
   // descriptor, tiles and tables on the host, then copied into the array on the caller's stream
   TubeDev d{};
@@ -1222,29 +1234,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
   std::vector<int2> tiles(ntiles);
   for (int k = 0; k < ntiles; ++k) tiles[k] = make_int2(0, k * TX);
   std::vector<double> tab(tab_size(t.Qp, t.Qxi), 0.0), pb(t.Qp), wp(t.Qp), xi(t.Qxi), wxi(t.Qxi);
-  if (!rlbq::gauss_laguerre1(t.Qp, pb.data(), wp.data()) || !rlbq::gauss_legendre(t.Qxi, xi.data(), wxi.data()))
-    return RLB_EINVAL;
-  for (int i = 0; i < t.Qp; ++i) {
-    tab[TAB_PBAR + i] = pb[i];
-    tab[TAB_PBAR2 + i] = pb[i] * pb[i];
-    tab[TAB_WP + i] = wp[i];
-    for (int q = 0; q <= t.Np; ++q) {  // K[i][q] = (-1)^q sum_{l=q}^{Np} C(l, q) L^(1)_l(pbar_i)
-      long double acc = 0.0L;
-      for (int l = q; l <= t.Np; ++l) {
-        long double C = 1.0L;
-        for (int u = 1; u <= q; ++u) C = C * (l - q + u) / u;
-        acc += C * rlbq::laguerre1(l, pb[i]);
-      }
-      tab[TAB_K + i * (NP_MAX + 1) + q] = (double)((q % 2) ? -acc : acc);
-    }
-  }
-  for (int j = 0; j < t.Qxi; ++j) {
-    tab[TAB_XI + j] = xi[j];
-    for (int k = 0; k <= NV_MAX; ++k)
-      tab[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
-    for (int st = 0; st < 3; ++st) tab[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
-  }
-  fill_eps(tab.data() + tab_eps(t.Qxi), t.Qp, t.Qxi, wp.data(), wxi.data());
+  if (!fill_tube_tables(t, pb.data(), wp.data(), xi.data(), wxi.data(), tab.data())) return RLB_EINVAL;
   RLB_CUDA(cudaMemcpyAsync(b, &d, sizeof(TubeDev), cudaMemcpyHostToDevice, s));
   RLB_CUDA(cudaMemcpyAsync(b + off_tiles, tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice, s));
   RLB_CUDA(cudaMemcpyAsync(b + off_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s));

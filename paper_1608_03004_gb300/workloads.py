@@ -18,6 +18,8 @@ Workloads (sizes as stated):
     relative amplitude 0.05, n = P, v = 0.
   * ``stress``: one Sod tube, Nx = 1,048,576, Qxi = 128 (384 velocities), tau = 1e-2.
   * ``random_smooth``: seeded smooth periodic (P, n, v) profiles for parity tests.
+  * ``fast_flow``: smooth periodic states whose speed reaches vmax (0.9 .. 0.99), where the Landau-frame
+    extraction of e and u^mu cancels; ``rarefied``: P and n down to 1e-4 of their largest value.
 """
 from __future__ import annotations
 
@@ -138,6 +140,55 @@ def random_smooth(Nx: int, Qxi: int, tau: float, seed: int, bc: int = BC_PERIODI
     v = field(vmax)
     return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau, cfl), dx=dx, Qp=Qp, Np=Np, Nv=Nv, bc=bc,
                     x_left=0.0, P=P, n=n, v=v)
+
+
+def _stiff_for(vmax: float, limit: float = 1.8) -> float:
+    """dt / tau that keeps dt gamma (1 + vmax) / tau at `limit`, inside the SSP-RK3 + WENO5 stability bound
+    (1.977 at CFL 0.5) for every direction of a flow of speed vmax."""
+    return limit * math.sqrt(1.0 - vmax * vmax) / (1.0 + vmax)
+
+
+def fast_flow(Nx: int, Qxi: int, tau: float, vmax: float, seed: int, uniform: bool = False,
+              bc: int = BC_PERIODIC, stiff_limit: float = 0.25) -> TubeSpec:
+    """Smooth periodic states at speeds up to vmax: v = vmax sin(2 pi x + phase) (both directions) with P and n
+    varying by +-30 %, or with uniform=True a near-uniform flow v = vmax - 0.002 (1 + sin(2 pi x + phase)) with
+    P and n varying by +-5 %. The time step keeps dt gamma (1 + vmax) / tau at stiff_limit: near |v| = 1 the
+    collision rate gamma (1 - v xi) / tau grows with the speed it acts on, and steps at the linear stability
+    bound (1.8 here) run away within a few steps at |v| >= 0.97."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / Nx
+    x = (np.arange(Nx) + 0.5) * dx
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    amp = 0.05 if uniform else 0.3
+    P = 1.0 + amp * np.sin(2 * np.pi * x + ph[0])
+    n = 1.0 + amp * np.sin(4 * np.pi * x + ph[1])
+    if uniform:
+        v = vmax - 0.002 * (1.0 + np.sin(2 * np.pi * x + ph[2]))
+    else:
+        v = vmax * np.sin(2 * np.pi * x + ph[2])
+    return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau, stiff=_stiff_for(vmax, stiff_limit)), dx=dx,
+                    bc=bc, x_left=0.0, P=P, n=n, v=v)
+
+
+def rarefied(Nx: int, Qxi: int, tau: float, seed: int, floor: float = 1e-4, vmax: float = 0.3,
+             bc: int = BC_PERIODIC) -> TubeSpec:
+    """Smooth periodic states with rarefied cells: P = floor^(1/2 + sin(2 pi x + phase)/2) spans [floor, 1]
+    on a log scale, n = P / T with T = 1 + 0.2 sin(...), |v| <= vmax."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / Nx
+    x = (np.arange(Nx) + 0.5) * dx
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    P = floor ** (0.5 + 0.5 * np.sin(2 * np.pi * x + ph[0]))
+    T = 1.0 + 0.2 * np.sin(2 * np.pi * x + ph[1])
+    v = vmax * np.sin(2 * np.pi * x + ph[2])
+    return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau, stiff=_stiff_for(vmax)), dx=dx, bc=bc,
+                    x_left=0.0, P=P, n=P / T, v=v)
+
+
+def strong_shock(Nx: int, Qxi: int, tau: float, ratio: float = 0.01) -> TubeSpec:
+    """Riemann tube with P_R / P_L = ratio (the strongest shocks of the batched workload), the batch's n and
+    time-step rules."""
+    return sod_tube(Nx, Qxi, tau, left=(1.0, 1.0, 0.0), right=(ratio, ratio / 0.8, 0.0), stiff=STIFF_STRONG)
 
 
 def total_nodes(specs: Sequence[TubeSpec]) -> int:

@@ -5,7 +5,11 @@ FP64 parity bar. Cases: the paper's Sod tube at Nx = 400 over the whole run to t
 grids around the 63-cell tile, odd Qxi (a xi = 0 node), a cell centre on the membrane, periodic grids,
 moving smooth states, the ballistic regime, high and low quadrature / truncation orders, mixed batches,
 and the full relaxation-time sweep (Nx = 4096, 28 tubes) in the launch configuration of the benchmark,
-checked on one-step windows the oracle recomputes.
+checked on one-step windows the oracle recomputes. The regime where the Landau-frame extraction cancels is
+covered separately: flows at |v| = 0.9 .. 0.99, rarefied cells (P and n down to 1e-4) and strong shocks
+(P_R / P_L = 0.01), each at the same 1e-12 bar, plus the two limits of the method: where the truncated
+equilibrium itself turns non-physical (both sides flag the same step) and where the kernel's Legendre series
+stops converging (|v| > 0.9955, refused).
 """
 import math
 
@@ -86,6 +90,67 @@ def test_truncation_orders(Qp, Np, Nv, Qxi):
 @pytest.mark.parametrize("vmax", [0.3, 0.7])
 def test_moving_smooth_states(vmax):
     check([W.random_smooth(150, 16, 2e-2, seed=int(vmax * 10), vmax=vmax)], 12)
+
+
+@pytest.mark.parametrize("vmax", [0.9, 0.95, 0.97])
+def test_fast_flows_both_directions(vmax):
+    """v = vmax sin(2 pi x + phase), P and n +-30 %, collisions active (dt gamma (1 + vmax) / tau = 0.25)."""
+    check([W.fast_flow(128, 16, 2e-2, vmax, seed=int(vmax * 100))], 3)
+
+
+@pytest.mark.parametrize("vmax", [0.95, 0.99])
+def test_fast_uniform_flows(vmax):
+    """Near-uniform flows at |v| = vmax - 0.002 (1 + sin): e = 3P is a small remainder of T^00 ~ 4 gamma^2 P
+    (gamma^2 = 50 at 0.99)."""
+    check([W.fast_flow(128, 16, 2e-2, vmax, seed=int(vmax * 100) + 1, uniform=True)], 3)
+
+
+def test_rarefied_cells():
+    """P from 1 down to 1e-4 on a log scale, T within +-20 %, |v| <= 0.3: the pointwise check of the positive
+    fields holds the rarefied cells to their own magnitude."""
+    check([W.rarefied(128, 16, 1e-2, seed=6)], 6)
+
+
+@pytest.mark.parametrize("tau", [1e-3, 1e-2])
+def test_strong_shock(tau):
+    """P_R / P_L = 0.01 (the batched workload's strongest shocks), 20 steps."""
+    check([W.strong_shock(200, 16, tau)], 20)
+
+
+def test_nonphysical_where_the_oracle_is():
+    """A full-period profile at |v| up to 0.99 stepped at dt gamma (1 + |v|) / tau = 1.8, inside the linear
+    stability bound of the scheme (1.977) but not near |v| = 1, where the collision rate grows with the speed
+    it relaxes: the oracle's first step is physical (every stage input keeps (T^00 + T^xx)^2 - 4 (T^0x)^2 >=
+    1e-4 (T^00 + T^xx)^2) and its second step fails in its second stage by -5.8e-4 of the same scale. The
+    kernel must agree: no flag after one step, RLB_ENONPHYS during the second."""
+    s = W.fast_flow(128, 16, 2e-2, 0.99, seed=3, stiff_limit=1.8)
+    p = H.to_params(s)
+    F1 = oracle.step(p, H.oracle_init(s), 1)
+    with pytest.raises(oracle.OracleError):
+        oracle.step(p, F1, 1)
+    with H.gpu_init([s]) as h:
+        rb.rlb_step(h, 1)
+        rb.rlb_sync(h)
+        H.assert_state_parity(H.split_state([s], rb.rlb_get_state(h))[0], F1, what="first step")
+        rb.rlb_step(h, 1)
+        with pytest.raises(rb.RlbError) as ei:
+            rb.rlb_sync(h)
+        assert ei.value.status == rb.ENONPHYS
+
+
+def test_speed_beyond_the_series_limit_is_refused():
+    """The kernel sums the Legendre series of (1 - v xi)^-m up to 16383 terms, which converges for |v| up to
+    0.99552: an initial state faster than that cannot be built (RLB_EINVAL), one just inside it can."""
+    for v0, ok in ((0.995, True), (0.996, False)):
+        s = W.fast_flow(64, 8, 2e-2, v0 + 0.002, seed=7, uniform=True)  # v in [v0 - 0.002, v0 + 0.002]
+        s.v = np.full(s.Nx, v0)
+        if ok:
+            with H.gpu_init([s]) as h:
+                H.assert_field_parity(rb.rlb_moments(h), oracle.fields(H.to_params(s), H.oracle_init(s)))
+        else:
+            with pytest.raises(rb.RlbError) as ei:
+                H.gpu_init([s])
+            assert ei.value.status == rb.EINVAL
 
 
 def test_ballistic():

@@ -2,14 +2,17 @@
 
 F is stored in FP32 or BF16; advection, equilibrium evaluation, collision and the Runge-Kutta combination run
 in FP32; the moments are compensated FP32 sums reduced in FP64 and the Landau frame is solved in FP64.
-Target: FP32 energy density within 1e-5 relative of the FP64 oracle, stated both as the mean over cells
-(|e - e_ref| / e_ref averaged) and as the worst cell; the worst cells sit on the shock and contact, where a
-shift of a fraction of a cell dominates (measured on the Sod run to t = 0.4, 444 steps: e mean 1.5e-6, worst
-1.9e-5; T^xx worst 3.3e-5), so the worst-cell bound is 5e-5. BF16 (unit roundoff 2^-8) loses several per
+Target: FP32 energy density within 1e-5 relative of the FP64 oracle, read normwise,
+max_x |e - e_ref| / max_x |e_ref|, and also held for the mean pointwise error (|e - e_ref| / e_ref averaged
+over cells). The worst single cell is recorded as well: on the Sod run to t = 0.4 (444 steps) it sits on the
+shock and contact, where a shift of a fraction of a cell dominates, at 1.9e-5 for e and 3.3e-5 for T^xx,
+above the target; it is bounded at 5e-5 to catch regressions. BF16 (unit roundoff 2^-8) loses several per
 cent on average and up to ~50 % at the waves over a few hundred steps (measured: e mean 6.0 %, T^xx mean
 5.3 %, worst T^xx 50.4 % on the contact): its rounding noise, relative 2^-9 of each weight-normalised
 population, is far above the limiter's sqrt(eps) = 1e-3, so the WENO weights follow the noise. Its errors
-are measured and bounded loosely. The errors found are printed (pytest -s).
+are measured and bounded loosely. The regime where the e, u^mu extraction cancels (flows at |v| up to 0.99,
+rarefied cells, strong shocks) has its own test that states both storages' errors there. The errors found
+are printed (pytest -s).
 """
 import math
 
@@ -38,18 +41,21 @@ def errors(f, ref):
     re = np.abs(f[E] - ref[E]) / np.abs(ref[E])
     rt = np.abs(f[TXX] - ref[TXX]) / np.abs(ref[TXX])
     return {
+        "e_norm": float(np.max(np.abs(f[E] - ref[E])) / np.max(np.abs(ref[E]))),
+        "Txx_norm": float(np.max(np.abs(f[TXX] - ref[TXX])) / np.max(np.abs(ref[TXX]))),
         "e_rel_mean": float(np.mean(re)), "e_rel_max": float(np.max(re)),
         "Txx_rel_mean": float(np.mean(rt)), "Txx_rel_max": float(np.max(rt)),
         "v_abs_max": float(np.max(np.abs(f[V] - ref[V]))),
     }
 
 
-# (mean bound, worst-cell bound) per storage
-BOUNDS = {rb.STORAGE_F32: (1e-5, 5e-5), rb.STORAGE_BF16: (0.1, 0.65)}
+# (normwise bound, mean pointwise bound, worst-cell bound) per storage; FP32's first two are the 1e-5 target
+BOUNDS = {rb.STORAGE_F32: (1e-5, 1e-5, 5e-5), rb.STORAGE_BF16: (0.25, 0.1, 0.65)}
 
 
 def check_bounds(err, storage):
-    mean_b, max_b = BOUNDS[storage]
+    norm_b, mean_b, max_b = BOUNDS[storage]
+    assert err["e_norm"] <= norm_b and err["Txx_norm"] <= norm_b, err
     assert err["e_rel_mean"] <= mean_b and err["Txx_rel_mean"] <= mean_b, err
     assert err["e_rel_max"] <= max_b and err["Txx_rel_max"] <= max_b and err["v_abs_max"] <= max_b, err
 
@@ -81,6 +87,30 @@ def test_moving_and_ballistic_batch_against_oracle(storage):
         err = errors(f, fr)
         print(f"storage {storage}: Nx={s.Nx} Qxi={s.Qxi} tau={s.tau} errors vs FP64 oracle {err}")
         check_bounds(err, storage)
+
+
+# the regime where the Landau-frame extraction cancels: (spec, steps); errors are stated for both storages
+HARD = [("fast flow, |v| <= 0.97", lambda: W.fast_flow(128, 16, 2e-2, 0.97, seed=97), 10),
+        ("near-uniform flow at |v| = 0.99", lambda: W.fast_flow(128, 16, 2e-2, 0.99, seed=100, uniform=True), 10),
+        ("rarefied cells, P down to 1e-4", lambda: W.rarefied(128, 16, 1e-2, seed=6), 40),
+        ("strong shock, P_R / P_L = 0.01", lambda: W.strong_shock(200, 16, 1e-2), 40)]
+# measured bounds in that regime (FP32: normwise e and T^xx within the 1e-5 target)
+HARD_BOUNDS = {rb.STORAGE_F32: (1e-5, 1e-4, 1e-3), rb.STORAGE_BF16: (0.25, 0.25, 1.0)}
+
+
+@pytest.mark.parametrize("storage", [rb.STORAGE_F32, rb.STORAGE_BF16])
+@pytest.mark.parametrize("case", range(len(HARD)))
+def test_hard_regime_errors_against_oracle(storage, case):
+    name, make, nsteps = HARD[case]
+    s = make()
+    (f,), _ = run([s], nsteps, storage)
+    _, fr = H.oracle_run(s, nsteps)
+    err = errors(f, fr)
+    print(f"storage {storage}: {name}, {nsteps} steps, errors vs FP64 oracle {err}")
+    norm_b, mean_b, max_b = HARD_BOUNDS[storage]
+    assert err["e_norm"] <= norm_b and err["Txx_norm"] <= norm_b, err
+    assert err["e_rel_mean"] <= mean_b and err["Txx_rel_mean"] <= mean_b, err
+    assert err["e_rel_max"] <= max_b and err["Txx_rel_max"] <= max_b, err
 
 
 def test_state_round_trip_rounds_to_storage():
