@@ -19,9 +19,12 @@ one gradient of the inverse problem on Gaussian bumps.
 solve); its roofline is HBM (algorithmic 8 x element size bytes per velocity node per step).
 
 --workload gradient: one gradient of the inverse problem on Gaussian bumps (Nx = 2048, Q = 3 x 32, 1000 steps,
-tau = 0.08 against the T^00 profile of tau* = 0.05, checkpoints every 50 steps) with respect to log(tau) and the
-initial fields, through the adjoint; gradient_batch: 64 such tubes (bump seeds 4 .. 67) in one handle. A step
-is one gradient; one update = one velocity node carried one time step forward and back.
+checkpoints every 50 steps): the loss is 1/2 |e(x) - e*(x)|^2 of the final energy density at tau = 0.08
+against the run at tau* = 0.05 from the initial pressure perturbed by a second set of Gaussian bumps
+(amplitude 0.05); the gradient is taken with respect to log(tau) and the initial fields, through the adjoint
+(rlb_fields_vjp carries dL/de through the Landau frame); gradient_batch: 64 such tubes (bump seeds 4 .. 67)
+in one handle. A step is one gradient; one update = one velocity node carried one time step forward and
+back.
 
 Prints one JSON line. Under torchrun every rank advances its own copy of the workload (weak scaling, no
 collective on the data path); the time is the max over ranks.
@@ -75,6 +78,7 @@ REF_BUDGET_S = 120.0  # the reference arm's whole run (warm-up and timed steps) 
 GRAD_METRIC = "G velocity-node gradient updates/s"
 GRAD_UNIT = "G gradient updates/s"
 GRAD_STEPS, GRAD_EVERY, GRAD_TAU, GRAD_TAU_STAR = 1000, 50, 0.08, 0.05
+GRAD_TARGET_SEED = 5  # bumps of the target's initial pressure perturbation (tube k: seed 5 + k)
 GRAD_CPU_STEPS = 4  # steps of each oracle run in the gradient workloads' CPU samples (two runs per gradient)
 # Algorithmic FP64 flops per velocity node per adjoint stage (FMA = 2, a division counted as one flop):
 # WENO5 interface derivative 130 (candidates 16, indicator terms 18, eps + beta_k 18, alpha_k and weights 11,
@@ -99,13 +103,16 @@ def workload(name: str, nx: int | None = None, ntubes: int | None = None):
                                    "dt=min(0.5dx,0.45tau), open BC")
     if name == "gradient":
         return [W.gaussian_bumps(tau=GRAD_TAU)], ("inverse problem on Gaussian bumps: Nx=2048, Qp=3, Qxi=32, "
-                                                  "Np=2, Nv=5, dt=0.5dx, open BC, tau=0.08 against the T00 profile "
-                                                  "of tau*=0.05, 1000 steps, checkpoints every 50")
+                                                  "Np=2, Nv=5, dt=0.5dx, open BC; loss 1/2 |e(x) - e*(x)|^2 of the "
+                                                  "final energy density at tau=0.08 against the run at tau*=0.05 "
+                                                  "from P perturbed by Gaussian bumps (amplitude 0.05, seed 5); "
+                                                  "1000 steps, checkpoints every 50, FP64")
     if name == "gradient_batch":
         m = ntubes or 64
         return [W.gaussian_bumps(tau=GRAD_TAU, seed=4 + k) for k in range(m)], (
             f"{m} inverse problems on Gaussian bumps (seeds 4..{3 + m}): Nx=2048, Qp=3, Qxi=32, Np=2, Nv=5, "
-            "dt=0.5dx, open BC, tau=0.08 against the T00 profiles of tau*=0.05, 1000 steps, checkpoints every 50")
+            "dt=0.5dx, open BC, e(x) at tau=0.08 against the runs at tau*=0.05 from perturbed P (seeds "
+            f"5..{4 + m}), 1000 steps, checkpoints every 50")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -375,7 +382,7 @@ def _oracle_fd_gradient_task(spec, nsteps: int) -> float:
     p = oracle.params(Qp=spec.Qp, Qxi=spec.Qxi, Np=spec.Np, Nv=spec.Nv, Nx=spec.Nx, dx=spec.dx, dt=spec.dt,
                       tau=spec.tau, bc=spec.bc)
     t0 = time.perf_counter()
-    og.grad_log_tau(p, spec.P, spec.n, spec.v, nsteps, lambda m: 0.5 * float(np.sum(m[2] ** 2)))
+    og.grad_log_tau(p, spec.P, spec.n, spec.v, nsteps, lambda m: 0.5 * float(np.sum(m[5] ** 2)), rows=8)
     return time.perf_counter() - t0
 
 
@@ -394,7 +401,7 @@ def oracle_gradient_sample(specs, nsteps: int):
         list(ex.map(_oracle_fd_gradient_task, sample, [nsteps] * len(sample)))
         wall = time.perf_counter() - t0
     nodes = W.total_nodes(sample)
-    what = (f"dL/dlog(tau) by central differences of the plain C FP64 oracle (two forward runs of {nsteps} "
+    what = (f"dL/dlog(tau) of a loss of e(x) by central differences of the plain C FP64 oracle (two forward runs of {nsteps} "
             f"steps) on {len(sample)} of the workload's tubes ({nodes} velocity nodes), one process per tube")
     return nodes * nsteps / wall / 1e9, len(sample), what
 
@@ -635,16 +642,19 @@ def run_gradient(args, specs, desc, rank, world, emit=True):
         if world > 1:
             torch.distributed.barrier()
 
-    with rb.rlb_init([mk(s, GRAD_TAU_STAR) for s in specs], Pd, nd, vd) as hs:  # the target profiles
+    # the targets: runs at tau* from the initial pressure perturbed by a second seed-fixed set of bumps
+    tg = [W.perturbed(s, seed=GRAD_TARGET_SEED + k) for k, s in enumerate(specs)]
+    Pt_, nt_, vt_ = (torch.tensor(np.concatenate([getattr(s, a) for s in tg]), **f64) for a in ("P", "n", "v"))
+    with rb.rlb_init([mk(s, GRAD_TAU_STAR) for s in specs], Pt_, nt_, vt_) as hs:
         rb.rlb_step(hs, GRAD_STEPS)
         ft = torch.empty((rb.NFIELDS, hs.nx_total), **f64)
         rb.rlb_moments(hs, ft)
-        target = ft[2].clone()
+        target = ft[rb.F_E].clone()
     h = rb.rlb_init(tubes, Pd, nd, vd)
     F0 = torch.empty(h.state_size, **f64)
     rb.rlb_get_state(h, F0)
     fields = torch.empty((rb.NFIELDS, h.nx_total), **f64)
-    gm = torch.zeros((5, h.nx_total), **f64)
+    gm = torch.zeros((rb.NFIELDS, h.nx_total), **f64)
     seed, gF = torch.empty(h.state_size, **f64), torch.empty(h.state_size, **f64)
     gP, gn, gv = (torch.empty(h.nx_total, **f64) for _ in range(3))
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -657,8 +667,8 @@ def run_gradient(args, specs, desc, rank, world, emit=True):
         if e:
             e[1].record(stream)
         rb.rlb_moments(h, fields)
-        torch.sub(fields[2], target, out=gm[2])  # dL/dT^00 of L = 1/2 sum (T^00 - target)^2
-        rb.rlb_moments_vjp(h, gm, seed)
+        torch.sub(fields[rb.F_E], target, out=gm[rb.F_E])  # dL/de of L = 1/2 sum (e - target)^2
+        rb.rlb_fields_vjp(h, gm, seed)
         if e:
             e[2].record(stream)
         _, glt = rb.rlb_backward(h, seed, gF)
@@ -696,8 +706,8 @@ def run_gradient(args, specs, desc, rank, world, emit=True):
     def user_gradient():
         lt = torch.full((len(tubes),), math.log(GRAD_TAU), dtype=torch.float64, requires_grad=True)
         Pt, nt, vt = (a.to("cuda", non_blocking=True).requires_grad_() for a in (Ph, nh, vh))
-        M = adjoint.run_moments(lt, Pt, nt, vt, tubes, GRAD_STEPS, args.every)
-        (0.5 * ((M[2] - target) ** 2).sum()).backward()
+        f = adjoint.run_fields(lt, Pt, nt, vt, tubes, GRAD_STEPS, args.every)
+        (0.5 * ((f[rb.F_E] - target) ** 2).sum()).backward()
         return [lt.grad.numpy(), Pt.grad.cpu().numpy(), nt.grad.cpu().numpy(), vt.grad.cpu().numpy()]
 
     user_gradient()  # warm-up: the first call loads torch's kernels for the loss and its backward

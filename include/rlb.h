@@ -55,7 +55,12 @@ typedef enum {
   RLB_ENONPHYS = 4  /* some cell reached a non-physical state since the last check */
 } rlb_status;
 
-enum { RLB_BC_OPEN = 0, RLB_BC_PERIODIC = 1 };
+/* Boundary of a tube. RLB_BC_OPEN: three zero-gradient ghost cells per side (section "Riemann problem").
+ * RLB_BC_PERIODIC: the tube wraps around. RLB_BC_HALO_LEFT / RLB_BC_HALO_RIGHT (flags, either or both, the
+ * other side open): the tube is one x-slab of a longer tube split over several tubes, handles or GPUs; the
+ * three ghost cells on that side are the neighbouring slab's edge cells, which the caller moves with
+ * rlb_halo_pack / rlb_halo_unpack before every stage (rlb_stage). */
+enum { RLB_BC_OPEN = 0, RLB_BC_PERIODIC = 1, RLB_BC_HALO_LEFT = 2, RLB_BC_HALO_RIGHT = 4 };
 
 /* Storage of F. FP64: everything in FP64 (the parity path). FP32 / BF16: F stored in that type, advection,
  * equilibrium evaluation, collision and the Runge-Kutta combination in FP32, the moments accumulated with
@@ -78,7 +83,7 @@ typedef struct {
   double dx;        /* cell width; cell c has its centre at x_left + (c + 1/2) dx */
   double dt;        /* time step */
   double tau;       /* relaxation time */
-  int32_t bc;       /* RLB_BC_OPEN (zero-gradient ghosts, section "Riemann problem") or RLB_BC_PERIODIC */
+  int32_t bc;       /* RLB_BC_OPEN, RLB_BC_PERIODIC, or RLB_BC_HALO_LEFT and/or RLB_BC_HALO_RIGHT */
   int32_t storage;  /* RLB_STORAGE_F64 (0), RLB_STORAGE_F32 or RLB_STORAGE_BF16; the same for every tube */
 } rlb_tube;
 
@@ -111,11 +116,48 @@ rlb_status rlb_init_riemann(rlb_handle *out, const rlb_tube *tubes, int32_t ntub
 rlb_status rlb_step(rlb_handle h, int64_t nsteps);
 
 /*
+ * Domain decomposition: one tube split into x-slabs (the method's one exchange step, section "Numerical
+ * results": WENO5 reaches three cells on each side, so every Runge-Kutta stage needs the neighbouring slabs'
+ * three edge cells of all Q velocities). A slab is a tube with RLB_BC_HALO_LEFT and/or RLB_BC_HALO_RIGHT; its
+ * handle keeps the ghost cells beside each row. The caller runs each step as three stages and, before each
+ * stage, moves the edge cells of that stage's input between neighbours (in one process, between handles of
+ * one GPU, or between GPUs with NCCL or peer copies):
+ *     for stage in 0, 1, 2:  rlb_halo_pack(h, stage, send); <send / receive>; rlb_halo_unpack(h, stage, recv);
+ *                            rlb_stage(h, stage);
+ * Buffer layout (elements of the handle's storage type, rlb_halo_size() of them): for every slab of the handle,
+ * in tube order, a block of Q x 3 elements per halo side, left side first; a block holds, row s by row s, three
+ * cells in ascending x. rlb_halo_pack writes a left block with the slab's cells 0, 1, 2 (for the left
+ * neighbour's right ghosts) and a right block with cells Nx-3, Nx-2, Nx-1 (for the right neighbour's left
+ * ghosts); rlb_halo_unpack reads a left block as the ghost cells -3, -2, -1 (the left neighbour's last three
+ * cells) and a right block as Nx, Nx+1, Nx+2 (the right neighbour's first three). A slab result is bit-identical
+ * to the same cells of the undivided tube. Slabs need Nx >= 3; rlb_step, rlb_autotune and the adjoint entry
+ * points return RLB_EINVAL for handles with slabs.
+ */
+
+/* rlb_halo_size - elements of the exchange buffer of a handle (0 without slabs). */
+int64_t rlb_halo_size(rlb_handle h);
+
+/* rlb_halo_pack - write the edge cells of stage `stage`'s input (0: the state, 1 and 2: the intermediate
+ *   Runge-Kutta states) into send (device pointer, rlb_halo_size() elements of the storage type). Ordered on
+ *   the handle's stream, asynchronous. */
+rlb_status rlb_halo_pack(rlb_handle h, int32_t stage, void *send);
+
+/* rlb_halo_unpack - set the ghost cells of stage `stage`'s input from recv (device pointer, same layout).
+ *   Ordered on the handle's stream, asynchronous. */
+rlb_status rlb_halo_unpack(rlb_handle h, int32_t stage, const void *recv);
+
+/* rlb_stage - run Runge-Kutta stage `stage` (0, 1, 2) of the current step for every tube of the handle (one
+ *   stage kernel launch; the three in order make one rlb_step). Asynchronous on the handle's stream. */
+rlb_status rlb_stage(rlb_handle h, int32_t stage);
+
+/*
  * rlb_moments - write the macroscopic fields of the current state (section "Relativistic lattice
  *   Boltzmann equation"): N^0, N^x, T^00, T^0x, T^xx, the Landau-frame energy density e, velocity v and
  *   density n = -u_mu N^mu, as [RLB_NFIELDS][sum_b Nx_b] doubles into out (device pointer if
  *   out_on_device, else host; a host copy waits for the stream). Returns RLB_ENONPHYS if the sticky flag
- *   is set (the fields are still written).
+ *   is set (the fields are still written). With FP32/BF16 storage the moments of tubes with collisions are
+ *   the compensated sums the last stage accumulated while storing F (double-float, about 1e-13 relative to
+ *   the exact sums of the stored F); ballistic tubes are summed over F in FP64.
  */
 rlb_status rlb_moments(rlb_handle h, double *out, int32_t out_on_device);
 
@@ -261,7 +303,7 @@ rlb_status rlb_step_static(const rlb_tube *tube, const double *F_in, double *F_o
  * (P, n, v) and log(tau) of every tube, by the exact transpose of each stage of the discrete step (WENO5
  * flux differences, Anderson-Witting collision with the equilibrium of Eq. (feqtrunc) through the Landau
  * frame, SSP-RK3 combination) evaluated in FP64 on the GPU. The time step dt of a tube is held fixed.
- * Handles with reduced-precision storage return RLB_EINVAL from all four.
+ * Handles with reduced-precision storage return RLB_EINVAL from all five.
  * Layouts: "packed state" = the layout of rlb_get_state (per tube [Q][Nx] doubles, tube after tube);
  * "field layout" = [sum of Nx] doubles, tube after tube. All pointers below are device pointers unless
  * stated; the calls run on the handle's stream and return after their work has finished.
@@ -300,6 +342,20 @@ rlb_status rlb_backward(rlb_handle h, const double *seed, double *grad_state, do
  *                 Boltzmann equation").
  */
 rlb_status rlb_moments_vjp(rlb_handle h, const double *grad_moments, double *seed);
+
+/*
+ * rlb_fields_vjp - seed of rlb_backward from the adjoint of all the fields of rlb_moments at the handle's
+ *   current state (after rlb_record, the state after the recorded steps):
+ *   grad_fields:  [RLB_NFIELDS][sum of Nx] (field layout per row, rows as in rlb_moments: N^0, N^x, T^00,
+ *                 T^0x, T^xx, e, v, n), read only.
+ *   seed:         packed state, written with dL/dF_s(x) = sum_a G_a(x) c_a(s), c as in rlb_moments_vjp, where
+ *                 G_a = dL/dM_a + dL/de de/dM_a + dL/dv dv/dM_a + dL/dn dn/dM_a: the derivatives of the
+ *                 Landau-frame solution (section "Relativistic lattice Boltzmann equation", T^mu_nu u^nu =
+ *                 -e u^mu, n = -u_mu N^mu) at each cell's moments.
+ *   Returns RLB_EINVAL for NULL pointers or reduced storage, RLB_ENONPHYS if a cell's moments have no Landau
+ *   frame (its seed then carries only the moments' share).
+ */
+rlb_status rlb_fields_vjp(rlb_handle h, const double *grad_fields, double *seed);
 
 /*
  * rlb_init_vjp - adjoint of the initial condition of rlb_init (F = F^eq of Eq. (feqtrunc) with T = P/n and

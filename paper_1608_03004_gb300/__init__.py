@@ -33,15 +33,20 @@ from .binding import (  # noqa: F401
     rlb_error_string,
     rlb_get_launch,
     rlb_get_state,
+    rlb_halo_pack,
+    rlb_halo_size,
+    rlb_halo_unpack,
     rlb_init,
     rlb_init_riemann,
     rlb_init_vjp,
     rlb_moments,
+    rlb_fields_vjp,
     rlb_moments_vjp,
     rlb_quadrature,
     rlb_record,
     rlb_set_launch,
     rlb_set_state,
+    rlb_stage,
     rlb_state_size,
     rlb_step,
     rlb_step_static,

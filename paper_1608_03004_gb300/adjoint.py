@@ -1,12 +1,12 @@
 """Gradients of a run of the time step, through torch.autograd.
 
 A run starts from the truncated equilibrium of per-cell fields (P, n, v) (Eq. (condinit) with Eq. (feqtrunc))
-and takes nsteps SSP-RK3 steps of Eq. (Boltz) with each tube's time step held fixed; its output is the five
-conserved moments (N^0, N^x, T^00, T^0x, T^xx) of every cell. The backward pass is the library's hand-written
-adjoint: rlb_record keeps a checkpoint every `every` steps, rlb_backward recomputes each segment from its
-checkpoint and runs the transposed stage kernels backwards, rlb_moments_vjp seeds it from the moments'
-gradient and rlb_init_vjp carries the result back to (P, n, v). Argument marshalling only: every step runs in
-the CUDA library.
+and takes nsteps SSP-RK3 steps of Eq. (Boltz) with each tube's time step held fixed; its output is the fields
+of every cell: the five conserved moments (N^0, N^x, T^00, T^0x, T^xx) and the Landau-frame e, v, n. The
+backward pass is the library's hand-written adjoint: rlb_record keeps a checkpoint every `every` steps,
+rlb_backward recomputes each segment from its checkpoint and runs the transposed stage kernels backwards,
+rlb_fields_vjp seeds it from the fields' gradient (through the Landau frame on the device) and rlb_init_vjp
+carries the result back to (P, n, v). Argument marshalling only: every step runs in the CUDA library.
 """
 from __future__ import annotations
 
@@ -38,14 +38,14 @@ class _Run(torch.autograd.Function):
         ctx.h = h
         ctx.lt_device = log_tau.device
         ctx.save_for_backward(P_, n_, v_)
-        return fields[:5].clone()
+        return fields
 
     @staticmethod
-    def backward(ctx, grad_m):
+    def backward(ctx, grad_f):
         h = ctx.h
         P, n, v = ctx.saved_tensors
         seed = torch.empty(h.state_size, dtype=torch.float64, device=P.device)
-        rb.rlb_moments_vjp(h, grad_m.contiguous(), seed)
+        rb.rlb_fields_vjp(h, grad_f.contiguous(), seed)
         gF = torch.empty_like(seed)
         _, glt = rb.rlb_backward(h, seed, gF)
         gP, gn, gv = torch.empty_like(P), torch.empty_like(n), torch.empty_like(v)
@@ -55,8 +55,14 @@ class _Run(torch.autograd.Function):
         return (torch.as_tensor(glt, dtype=torch.float64, device=ctx.lt_device), gP, gn, gv, None, None, None)
 
 
-def run_moments(log_tau, P, n, v, tubes: Sequence[rb.Tube], nsteps: int, every: int = 50):
-    """Conserved moments [5][sum Nx] after nsteps steps from F = F^eq(P, n, v), differentiable in log_tau
-    ([ntubes], float64) and in P, n, v ([sum Nx] float64 CUDA tensors, tube after tube). Each tube's
-    relaxation time is exp(log_tau[b]) (inf: ballistic); its dt is taken from `tubes` and held fixed."""
+def run_fields(log_tau, P, n, v, tubes: Sequence[rb.Tube], nsteps: int, every: int = 50):
+    """Fields [RLB_NFIELDS][sum Nx] (N^0, N^x, T^00, T^0x, T^xx, e, v, n) after nsteps steps from
+    F = F^eq(P, n, v), differentiable in log_tau ([ntubes], float64) and in P, n, v ([sum Nx] float64 CUDA
+    tensors, tube after tube). Each tube's relaxation time is exp(log_tau[b]) (inf: ballistic); its dt is taken
+    from `tubes` and held fixed."""
     return _Run.apply(log_tau, P, n, v, list(tubes), int(nsteps), int(every))
+
+
+def run_moments(log_tau, P, n, v, tubes: Sequence[rb.Tube], nsteps: int, every: int = 50):
+    """The five conserved moments [5][sum Nx] of run_fields."""
+    return run_fields(log_tau, P, n, v, tubes, nsteps, every)[:5]

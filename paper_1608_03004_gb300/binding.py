@@ -17,11 +17,12 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ENONPHYS = 0, 1, 2, 3, 4
-BC_OPEN, BC_PERIODIC = 0, 1
+BC_OPEN, BC_PERIODIC, BC_HALO_LEFT, BC_HALO_RIGHT = 0, 1, 2, 4
 STORAGE_F64, STORAGE_F32, STORAGE_BF16 = 0, 1, 2
 STORAGE = {"f64": STORAGE_F64, "f32": STORAGE_F32, "bf16": STORAGE_BF16}
 FIELDS = ("N0", "Nx", "T00", "T0x", "Txx", "e", "v", "n")
 NFIELDS = len(FIELDS)
+F_N0, F_NX, F_T00, F_T0X, F_TXX, F_E, F_V, F_N = range(NFIELDS)
 
 _lib = None
 _lock = threading.Lock()
@@ -117,6 +118,11 @@ def load():
             "rlb_warnings": ([vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
             "rlb_backward": ([vp, vp, vp, dp], ctypes.c_int),
             "rlb_moments_vjp": ([vp, vp, vp], ctypes.c_int),
+            "rlb_fields_vjp": ([vp, vp, vp], ctypes.c_int),
+            "rlb_halo_size": ([vp], ctypes.c_int64),
+            "rlb_halo_pack": ([vp, ctypes.c_int32, vp], ctypes.c_int),
+            "rlb_halo_unpack": ([vp, ctypes.c_int32, vp], ctypes.c_int),
+            "rlb_stage": ([vp, ctypes.c_int32], ctypes.c_int),
             "rlb_init_vjp": ([vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -341,6 +347,43 @@ def rlb_step_static(tube: Tube, F_in, F_out, nsteps: int, flag=None, stream=None
                                   _stream(stream)), "rlb_step_static")
 
 
+def halo_dtype(h: Handle):
+    """torch dtype of a handle's exchange buffer (its storage type)."""
+    import torch
+
+    return {STORAGE_F64: torch.float64, STORAGE_F32: torch.float32, STORAGE_BF16: torch.bfloat16}[h.tubes[0].storage]
+
+
+def rlb_halo_size(h: Handle) -> int:
+    """Elements of the handle's exchange buffer (rlb_halo_size)."""
+    return int(load().rlb_halo_size(h.ptr))
+
+
+def _halo_buf(h: Handle, buf):
+    import torch
+
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous() or buf.dtype != halo_dtype(h):
+        raise ValueError("exchange buffers must be contiguous CUDA tensors of the handle's storage type")
+    if buf.numel() < rlb_halo_size(h):
+        raise ValueError(f"exchange buffer holds {buf.numel()} elements, {rlb_halo_size(h)} needed")
+    return ctypes.c_void_p(buf.data_ptr())
+
+
+def rlb_halo_pack(h: Handle, stage: int, send) -> None:
+    """Edge cells of stage `stage`'s input of every slab into send (rlb_halo_pack)."""
+    _check(load().rlb_halo_pack(h.ptr, int(stage), _halo_buf(h, send)), "rlb_halo_pack")
+
+
+def rlb_halo_unpack(h: Handle, stage: int, recv) -> None:
+    """Ghost cells of stage `stage`'s input of every slab from recv (rlb_halo_unpack)."""
+    _check(load().rlb_halo_unpack(h.ptr, int(stage), _halo_buf(h, recv)), "rlb_halo_unpack")
+
+
+def rlb_stage(h: Handle, stage: int) -> None:
+    """One Runge-Kutta stage of the current step (rlb_stage)."""
+    _check(load().rlb_stage(h.ptr, int(stage)), "rlb_stage")
+
+
 def rlb_get_launch(h: Handle) -> Launch:
     out = Launch()
     _check(load().rlb_get_launch(h.ptr, ctypes.byref(out)), "rlb_get_launch")
@@ -384,6 +427,14 @@ def rlb_moments_vjp(h: Handle, grad_moments, seed):
     """seed (packed, CUDA) = dL/dF from grad_moments [5][sum Nx] (CUDA): the adjoint of the five moments."""
     _check(load().rlb_moments_vjp(h.ptr, _dev_ptr(grad_moments, 5 * h.nx_total), _dev_ptr(seed, h.state_size)),
            "rlb_moments_vjp")
+    return seed
+
+
+def rlb_fields_vjp(h: Handle, grad_fields, seed):
+    """seed (packed, CUDA) = dL/dF from grad_fields [RLB_NFIELDS][sum Nx] (CUDA): the adjoint of the five
+    moments and of the Landau-frame e, v, n at the handle's current state."""
+    _check(load().rlb_fields_vjp(h.ptr, _dev_ptr(grad_fields, NFIELDS * h.nx_total),
+                                 _dev_ptr(seed, h.state_size)), "rlb_fields_vjp")
     return seed
 
 

@@ -162,10 +162,13 @@ __global__ void __launch_bounds__(NT) rlb_init_kernel(InitArgs A) {
     init_tile<S, NP_MAX, NV_MAX>(A, T, tl.y, sm);
 }
 
+// Fields of every cell: the five moments summed over F in FP64, or, with M != NULL, read from M for tubes with
+// collisions (reduced storage: the stage kernel leaves the FP64 moments of its output there, so F need not be
+// read again; ballistic tubes keep no moments and are summed), then the Landau frame.
 template <typename S>
 __global__ void __launch_bounds__(GW) rlb_fields_kernel(const TubeDev* tubes, const int2* tiles, const void* Fv,
                                                          const double* tabs, double* out, long long nxtot,
-                                                         int* flag) {
+                                                         int* flag, const double* M = nullptr) {
   const S* F = static_cast<const S*>(Fv);
   const int2 tl = tiles[blockIdx.x];
   const TubeDev T = tubes[tl.x];
@@ -174,7 +177,11 @@ __global__ void __launch_bounds__(GW) rlb_fields_kernel(const TubeDev* tubes, co
   const double* tab = tabs + T.tab;
   const S* f = F + T.off + x;
   double mom[5] = {0, 0, 0, 0, 0};
-  for (int j = 0; j < T.Qxi; ++j) {
+  if (M != nullptr && T.collide) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) mom[k] = M[k * nxtot + T.xoff + x];
+  }
+  for (int j = 0; j < ((M != nullptr && T.collide) ? 0 : T.Qxi); ++j) {
     double a = 0.0, b = 0.0;
     for (int i = 0; i < T.Qp; ++i) {
       const double v = ld_d<S>(f + (size_t)(i * T.Qxi + j) * T.ld);
@@ -208,6 +215,34 @@ template <typename S>
 __global__ void narrow_kernel(const double* src, S* dst, int ld, int Nx) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
   if (x < Nx) st_d<S>(dst + (size_t)r * ld + x, src[(size_t)r * Nx + x]);
+}
+
+// Exchange blocks of the slabs of a decomposed tube: one block of Q x 3 cells per halo side (left first), row
+// by row. pack: the slab's edge cells (0..2 on the left, Nx-3..Nx-1 on the right) into buf; unpack: buf into the
+// ghost cells beside each row (left ghosts -3..-1 at ld-3..ld-1, right ghosts Nx..Nx+2). Grid: x over the
+// 2 Q 3 cells of a slab's blocks, y over the slabs.
+struct HaloDesc {
+  int tube;
+  int bc;          // RLB_BC_HALO_LEFT and/or RLB_BC_HALO_RIGHT
+  long long off;   // first element of the slab's blocks in the buffer
+};
+
+template <typename S, bool PACK>
+__global__ void halo_kernel(const HaloDesc* hd, const TubeDev* tubes, S* F, S* buf) {
+  const HaloDesc d = hd[blockIdx.y];
+  const TubeDev T = tubes[d.tube];
+  const int Q = T.Qp * T.Qxi;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // side, row, cell
+  const int left = (d.bc & RLB_BC_HALO_LEFT) ? 1 : 0, sides = left + ((d.bc & RLB_BC_HALO_RIGHT) ? 1 : 0);
+  if (k >= sides * Q * HALO) return;
+  const int side = k / (Q * HALO), r = k - side * Q * HALO, s = r / HALO, c = r - s * HALO;
+  const bool is_left = left && side == 0;
+  S* row = F + T.off + (size_t)s * T.ld;
+  S* b = buf + d.off + k;
+  if (PACK)
+    *b = row[is_left ? c : T.Nx - HALO + c];
+  else
+    row[is_left ? T.ld - HALO + c : T.Nx + c] = *b;
 }
 
 #include "rlb_adjoint.cuh"
@@ -341,6 +376,10 @@ struct rlb_ctx {
   int2* d_atiles = nullptr;
   std::vector<int> atile_tube;
   double* d_dlt = nullptr;     // per adjoint tile: dL/dlog(tau)
+  // slabs of a decomposed tube: their exchange blocks (tube, sides, offset in the buffer)
+  std::vector<HaloDesc> halo;
+  HaloDesc* d_halo = nullptr;
+  long long halo_elems = 0;
 };
 
 namespace {
@@ -367,6 +406,7 @@ void free_ctx(rlb_ctx* h) {
   cudaFree(h->adj);
   cudaFree(h->d_atiles);
   cudaFree(h->d_dlt);
+  cudaFree(h->d_halo);
   cudaFree(h->d_tubes);
   cudaFree(h->d_tiles);
   cudaFree(h->d_wtiles);
@@ -460,8 +500,9 @@ std::vector<int2> build_tiles(const std::vector<rlb_tube>& tubes, int order, int
 rlb_status validate(const rlb_tube* t) {
   if (t->Qp < 3 || t->Qp > QP_MAX || t->Np < 2 || t->Np >= t->Qp || t->Np > NP_MAX) return RLB_EINVAL;
   if (t->Nv < 2 || t->Nv > NV_MAX || t->Qxi < 1 || t->Qxi > QXI_MAX || 2 * t->Qxi < t->Nv + 3) return RLB_EINVAL;
-  if (t->Nx < 1 || t->Nx > (1LL << 30) || (t->bc == RLB_BC_PERIODIC && t->Nx < 3)) return RLB_EINVAL;
-  if (t->bc != RLB_BC_OPEN && t->bc != RLB_BC_PERIODIC) return RLB_EINVAL;
+  if (t->Nx < 1 || t->Nx > (1LL << 30) || (t->bc != RLB_BC_OPEN && t->Nx < 3)) return RLB_EINVAL;
+  if (t->bc != RLB_BC_OPEN && t->bc != RLB_BC_PERIODIC && (t->bc & ~(RLB_BC_HALO_LEFT | RLB_BC_HALO_RIGHT)) != 0)
+    return RLB_EINVAL;
   if (!(t->dx > 0.0) || !std::isfinite(t->dx) || !(t->dt > 0.0) || !std::isfinite(t->dt)) return RLB_EINVAL;
   if (std::isnan(t->tau)) return RLB_EINVAL;
   if (t->storage != RLB_STORAGE_F64 && t->storage != RLB_STORAGE_F32 && t->storage != RLB_STORAGE_BF16)
@@ -502,7 +543,15 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
     d.bc = t.bc;
     d.collide = (t.tau > 0.0 && std::isfinite(t.tau)) ? 1 : 0;
     d.Nx = (int)t.Nx;
-    d.ld = (int)((t.Nx + 127) / 128 * 128);  // rows start on 256-byte boundaries for every storage type
+    // rows start on 256-byte boundaries for every storage type; a slab keeps its ghost cells beside each row
+    const bool slab = t.bc == RLB_BC_HALO_LEFT || t.bc == RLB_BC_HALO_RIGHT ||
+                      t.bc == (RLB_BC_HALO_LEFT | RLB_BC_HALO_RIGHT);
+    d.ld = (int)((t.Nx + (slab ? 2 * HALO : 0) + 127) / 128 * 128);
+    if (slab) {
+      const int sides = ((t.bc & RLB_BC_HALO_LEFT) ? 1 : 0) + ((t.bc & RLB_BC_HALO_RIGHT) ? 1 : 0);
+      h->halo.push_back(HaloDesc{b, t.bc, h->halo_elems});
+      h->halo_elems += (long long)sides * t.Qp * t.Qxi * HALO;
+    }
     d.storage = t.storage;
     d.off = off;
     d.xoff = xoff;
@@ -586,6 +635,11 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaMemsetAsync(h->F1, 0, h->esize * h->state_elems, h->stream));
   RLB_CUDA(cudaMemsetAsync(h->F2, 0, h->esize * h->state_elems, h->stream));
   RLB_CUDA(cudaMemsetAsync(h->d_flag, 0, 2 * sizeof(int), h->stream));
+  if (!h->halo.empty()) {
+    RLB_CUDA(cudaMalloc(&h->d_halo, sizeof(HaloDesc) * h->halo.size()));
+    RLB_CUDA(cudaMemcpyAsync(h->d_halo, h->halo.data(), sizeof(HaloDesc) * h->halo.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+  }
   rlb_status st = ensure_series_tables(h->dev);
   if (st != RLB_OK) return st;
   // resident CTAs per SM of this handle's stage kernel (the persistent grids' default size)
@@ -721,9 +775,8 @@ rlb_status rlb_init_riemann(rlb_handle* out, const rlb_tube* tubes, int32_t ntub
 
 namespace {
 
-// nsteps steps as plain launches on `stream`. in_graph: the launches belong to one captured graph, whose
-// counter-schedule launches get counters of their own (zeroed once up front), else each step zeroes three.
-rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in_graph) {
+// One stage st of the current step as one launch on `stream`, with work counter ctr (counter schedule).
+rlb_status launch_stage(rlb_ctx* h, cudaStream_t stream, int st, int* ctr) {
   const void* in[3] = {h->F, h->F1, h->F2};
   void* out[3] = {h->F1, h->F2, h->F};
   const int sched = h->cfg.schedule;
@@ -734,79 +787,88 @@ rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in
                        ? items
                        : std::max(1, std::min(items, h->nsm * (h->cfg.ctas_per_sm > 0 ? h->cfg.ctas_per_sm
                                                                                        : h->occupancy)));
+  if (h->storage == RLB_STORAGE_F64) {
+    StageArgs A{};
+    A.tubes = h->d_tubes;
+    A.tiles = h->d_tiles;
+    A.tab = h->d_tab;
+    A.flag = h->d_flag;
+    A.warn = h->d_flag + 1;
+    A.Fn = static_cast<const double*>(h->F);
+    A.Fin = static_cast<const double*>(in[st]);
+    A.Fout = static_cast<double*>(out[st]);
+    A.a = RK_A[st];
+    A.b = RK_B[st];
+    A.stage = st;
+    A.ntiles = h->ntiles;
+    A.schedule = sched;
+    A.counter = ctr;
+    A.split = split;
+    if (sched == RLB_SCHED_TILE)
+      rlb_stage_kernel<0><<<grid, NT, h->stage_smem, stream>>>(A);
+    else if (sched == RLB_SCHED_STRIDE)
+      rlb_stage_kernel<1><<<grid, NT, h->stage_smem, stream>>>(A);
+    else
+      rlb_stage_kernel<2><<<grid, NT, h->stage_smem, stream>>>(A);
+  } else {
+    const double* min[3] = {h->M, h->M1, h->M2};
+    double* mout[3] = {h->M1, h->M2, h->M};
+    StageArgsRP A{};
+    A.tubes = h->d_tubes;
+    A.wtiles = h->d_wtiles;
+    A.nwt = h->nwt;
+    A.tab = h->d_tab;
+    A.tabf = h->d_tabf;
+    A.flag = h->d_flag;  // two words: non-physical flag, warning bits
+    A.Fn = h->F;
+    A.nxtot = h->nxtot;
+    A.Fin = in[st];
+    A.Fout = out[st];
+    A.Min = min[st];
+    A.Mout = mout[st];
+    A.a = (float)RK_A[st];
+    A.b = (float)RK_B[st];
+    A.bd = RK_B[st];
+    A.stage = st;
+    A.ngroups = items;
+    A.schedule = sched;
+    A.counter = ctr;
+    A.brows = h->brows;
+    const size_t sb = rp_smem_bytes(h->brows);
+    if (h->storage == RLB_STORAGE_F32) {
+      if (sched == RLB_SCHED_TILE)
+        rlb_stage_rp_kernel<float, 0><<<grid, RP_NT, sb, stream>>>(A);
+      else if (sched == RLB_SCHED_STRIDE)
+        rlb_stage_rp_kernel<float, 1><<<grid, RP_NT, sb, stream>>>(A);
+      else
+        rlb_stage_rp_kernel<float, 2><<<grid, RP_NT, sb, stream>>>(A);
+    } else {
+      if (sched == RLB_SCHED_TILE)
+        rlb_stage_rp_kernel<__nv_bfloat16, 0><<<grid, RP_NT, sb, stream>>>(A);
+      else if (sched == RLB_SCHED_STRIDE)
+        rlb_stage_rp_kernel<__nv_bfloat16, 1><<<grid, RP_NT, sb, stream>>>(A);
+      else
+        rlb_stage_rp_kernel<__nv_bfloat16, 2><<<grid, RP_NT, sb, stream>>>(A);
+    }
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// nsteps steps as plain launches on `stream`. in_graph: the launches belong to one captured graph, whose
+// counter-schedule launches get counters of their own (zeroed once up front), else each step zeroes three.
+rlb_status launch_steps(rlb_ctx* h, cudaStream_t stream, int64_t nsteps, bool in_graph) {
+  const int sched = h->cfg.schedule;
   if (sched == RLB_SCHED_COUNTER && in_graph)
     RLB_CUDA(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 3 * nsteps, stream));
   for (int64_t t = 0; t < nsteps; ++t) {
     if (sched == RLB_SCHED_COUNTER && !in_graph) RLB_CUDA(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 3, stream));
     int* ctr = h->d_counters + (in_graph ? 3 * t : 0);
     for (int st = 0; st < 3; ++st) {
-      if (h->storage == RLB_STORAGE_F64) {
-        StageArgs A{};
-        A.tubes = h->d_tubes;
-        A.tiles = h->d_tiles;
-        A.tab = h->d_tab;
-        A.flag = h->d_flag;
-        A.warn = h->d_flag + 1;
-        A.Fn = static_cast<const double*>(h->F);
-        A.Fin = static_cast<const double*>(in[st]);
-        A.Fout = static_cast<double*>(out[st]);
-        A.a = RK_A[st];
-        A.b = RK_B[st];
-        A.stage = st;
-        A.ntiles = h->ntiles;
-        A.schedule = sched;
-        A.counter = ctr + st;
-        A.split = split;
-        if (sched == RLB_SCHED_TILE)
-          rlb_stage_kernel<0><<<grid, NT, h->stage_smem, stream>>>(A);
-        else if (sched == RLB_SCHED_STRIDE)
-          rlb_stage_kernel<1><<<grid, NT, h->stage_smem, stream>>>(A);
-        else
-          rlb_stage_kernel<2><<<grid, NT, h->stage_smem, stream>>>(A);
-      } else {
-        const double* min[3] = {h->M, h->M1, h->M2};
-        double* mout[3] = {h->M1, h->M2, h->M};
-        StageArgsRP A{};
-        A.tubes = h->d_tubes;
-        A.wtiles = h->d_wtiles;
-        A.nwt = h->nwt;
-        A.tab = h->d_tab;
-        A.tabf = h->d_tabf;
-        A.flag = h->d_flag;  // two words: non-physical flag, warning bits
-        A.Fn = h->F;
-        A.nxtot = h->nxtot;
-        A.Fin = in[st];
-        A.Fout = out[st];
-        A.Min = min[st];
-        A.Mout = mout[st];
-        A.a = (float)RK_A[st];
-        A.b = (float)RK_B[st];
-        A.bd = RK_B[st];
-        A.stage = st;
-        A.ngroups = items;
-        A.schedule = sched;
-        A.counter = ctr + st;
-        A.brows = h->brows;
-        const size_t sb = rp_smem_bytes(h->brows);
-        if (h->storage == RLB_STORAGE_F32) {
-          if (sched == RLB_SCHED_TILE)
-            rlb_stage_rp_kernel<float, 0><<<grid, RP_NT, sb, stream>>>(A);
-          else if (sched == RLB_SCHED_STRIDE)
-            rlb_stage_rp_kernel<float, 1><<<grid, RP_NT, sb, stream>>>(A);
-          else
-            rlb_stage_rp_kernel<float, 2><<<grid, RP_NT, sb, stream>>>(A);
-        } else {
-          if (sched == RLB_SCHED_TILE)
-            rlb_stage_rp_kernel<__nv_bfloat16, 0><<<grid, RP_NT, sb, stream>>>(A);
-          else if (sched == RLB_SCHED_STRIDE)
-            rlb_stage_rp_kernel<__nv_bfloat16, 1><<<grid, RP_NT, sb, stream>>>(A);
-          else
-            rlb_stage_rp_kernel<__nv_bfloat16, 2><<<grid, RP_NT, sb, stream>>>(A);
-        }
-      }
+      const rlb_status r = launch_stage(h, stream, st, ctr + st);
+      if (r != RLB_OK) return r;
     }
   }
-  return cuda_status(cudaGetLastError());
+  return RLB_OK;
 }
 
 // Capture graph_steps steps on the private stream (once per launch shape).
@@ -836,7 +898,7 @@ void drop_graph(rlb_ctx* h) {
 extern "C" {
 
 rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
-  if (!h || nsteps < 0) return RLB_EINVAL;
+  if (!h || nsteps < 0 || !h->halo.empty()) return RLB_EINVAL;
   DeviceGuard gd(h->dev);
   const int G = h->cfg.graph_steps;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -851,6 +913,46 @@ rlb_status rlb_step(rlb_handle h, int64_t nsteps) {
   RLB_CUDA(cudaEventRecord(h->ev_join, h->gstream));
   RLB_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   return st;
+}
+
+int64_t rlb_halo_size(rlb_handle h) { return h ? h->halo_elems : -1; }
+
+static rlb_status halo_copy(rlb_handle h, int32_t stage, void* buf, bool pack) {
+  if (!h || !buf || stage < 0 || stage > 2) return RLB_EINVAL;
+  if (h->halo.empty()) return RLB_OK;
+  DeviceGuard gd(h->dev);
+  void* Fs[3] = {h->F, h->F1, h->F2};
+  int most = 0;
+  for (const HaloDesc& d : h->halo) most = std::max(most, 2 * h->td[d.tube].Qp * h->td[d.tube].Qxi * HALO);
+  const dim3 grid((most + 255) / 256, (unsigned)h->halo.size());
+  if (h->storage == RLB_STORAGE_F64) {
+    double *F = static_cast<double*>(Fs[stage]), *b = static_cast<double*>(buf);
+    if (pack) halo_kernel<double, true><<<grid, 256, 0, h->stream>>>(h->d_halo, h->d_tubes, F, b);
+    else halo_kernel<double, false><<<grid, 256, 0, h->stream>>>(h->d_halo, h->d_tubes, F, b);
+  } else if (h->storage == RLB_STORAGE_F32) {
+    float *F = static_cast<float*>(Fs[stage]), *b = static_cast<float*>(buf);
+    if (pack) halo_kernel<float, true><<<grid, 256, 0, h->stream>>>(h->d_halo, h->d_tubes, F, b);
+    else halo_kernel<float, false><<<grid, 256, 0, h->stream>>>(h->d_halo, h->d_tubes, F, b);
+  } else {
+    __nv_bfloat16 *F = static_cast<__nv_bfloat16*>(Fs[stage]), *b = static_cast<__nv_bfloat16*>(buf);
+    if (pack) halo_kernel<__nv_bfloat16, true><<<grid, 256, 0, h->stream>>>(h->d_halo, h->d_tubes, F, b);
+    else halo_kernel<__nv_bfloat16, false><<<grid, 256, 0, h->stream>>>(h->d_halo, h->d_tubes, F, b);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+rlb_status rlb_halo_pack(rlb_handle h, int32_t stage, void* send) { return halo_copy(h, stage, send, true); }
+
+rlb_status rlb_halo_unpack(rlb_handle h, int32_t stage, const void* recv) {
+  return halo_copy(h, stage, const_cast<void*>(recv), false);
+}
+
+rlb_status rlb_stage(rlb_handle h, int32_t stage) {
+  if (!h || stage < 0 || stage > 2) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  if (h->cfg.schedule == RLB_SCHED_COUNTER)
+    RLB_CUDA(cudaMemsetAsync(h->d_counters + stage, 0, sizeof(int), h->stream));
+  return launch_stage(h, h->stream, stage, h->d_counters + stage);
 }
 
 rlb_status rlb_get_launch(rlb_handle h, rlb_launch* out) {
@@ -884,7 +986,7 @@ rlb_status rlb_set_launch(rlb_handle h, const rlb_launch* cfg) {
 }
 
 rlb_status rlb_autotune(rlb_handle h, int32_t trial_steps, rlb_launch* best, double* best_ms_per_step) {
-  if (!h || trial_steps < 1 || trial_steps > GRAPH_MAX) return RLB_EINVAL;
+  if (!h || trial_steps < 1 || trial_steps > GRAPH_MAX || !h->halo.empty()) return RLB_EINVAL;
   DeviceGuard gd(h->dev);
   // save the state (and, for reduced storage, the moments the first stage reads)
   const size_t fbytes = h->esize * h->state_elems;
@@ -953,10 +1055,10 @@ rlb_status rlb_moments(rlb_handle h, double* out, int32_t out_on_device) {
                                                                 h->nxtot, h->d_flag);
   else if (h->storage == RLB_STORAGE_F32)
     rlb_fields_kernel<float><<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab, dst,
-                                                               h->nxtot, h->d_flag);
+                                                               h->nxtot, h->d_flag, h->M);
   else
     rlb_fields_kernel<__nv_bfloat16><<<h->ntiles, GW, 0, h->stream>>>(h->d_tubes, h->d_tiles, h->F, h->d_tab, dst,
-                                                                       h->nxtot, h->d_flag);
+                                                                       h->nxtot, h->d_flag, h->M);
   RLB_CUDA(cudaGetLastError());
   if (!out_on_device)
     RLB_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * RLB_NFIELDS * h->nxtot, cudaMemcpyDeviceToHost, h->stream));
@@ -1186,7 +1288,7 @@ extern "C" rlb_status rlb_step_static(const rlb_tube* tube, const double* F_in, 
   if (!tube || !F_in || !F_out || nsteps < 0) return RLB_EINVAL;
   rlb_status st = validate(tube);
   if (st != RLB_OK) return st;
-  if (tube->storage != RLB_STORAGE_F64) return RLB_EINVAL;
+  if (tube->storage != RLB_STORAGE_F64 || (tube->bc != RLB_BC_OPEN && tube->bc != RLB_BC_PERIODIC)) return RLB_EINVAL;
   const rlb_tube& t = *tube;
   const int Q = t.Qp * t.Qxi, Nx = (int)t.Nx;
   const int ntiles = (Nx + TX - 1) / TX;
@@ -1369,7 +1471,7 @@ rlb_status padded_to_packed(rlb_ctx* h, const double* F, double* P) {
 extern "C" {
 
 rlb_status rlb_record(rlb_handle h, int64_t nsteps, int32_t every) {
-  if (!h || nsteps < 1 || every < 1 || h->storage != RLB_STORAGE_F64) return RLB_EINVAL;
+  if (!h || nsteps < 1 || every < 1 || h->storage != RLB_STORAGE_F64 || !h->halo.empty()) return RLB_EINVAL;
   DeviceGuard gd(h->dev);
   h->rec_steps = 0;
   h->rec_kept = false;
@@ -1417,7 +1519,7 @@ rlb_status rlb_record(rlb_handle h, int64_t nsteps, int32_t every) {
 }
 
 rlb_status rlb_backward(rlb_handle h, const double* seed, double* grad_state, double* grad_log_tau) {
-  if (!h || !seed || h->storage != RLB_STORAGE_F64 || h->rec_steps < 1) return RLB_EINVAL;
+  if (!h || !seed || h->storage != RLB_STORAGE_F64 || h->rec_steps < 1 || !h->halo.empty()) return RLB_EINVAL;
   DeviceGuard gd(h->dev);
   rlb_status st = ensure_adjoint_tiles(h);
   if (st != RLB_OK) return st;
@@ -1470,7 +1572,7 @@ rlb_status rlb_backward(rlb_handle h, const double* seed, double* grad_state, do
 }
 
 rlb_status rlb_moments_vjp(rlb_handle h, const double* grad_moments, double* seed) {
-  if (!h || !grad_moments || !seed || h->storage != RLB_STORAGE_F64) return RLB_EINVAL;
+  if (!h || !grad_moments || !seed || h->storage != RLB_STORAGE_F64 || !h->halo.empty()) return RLB_EINVAL;
   DeviceGuard gd(h->dev);
   rlb_status st = ensure_adjoint_tiles(h);
   if (st != RLB_OK) return st;
@@ -1481,9 +1583,21 @@ rlb_status rlb_moments_vjp(rlb_handle h, const double* grad_moments, double* see
   return RLB_OK;
 }
 
+rlb_status rlb_fields_vjp(rlb_handle h, const double* grad_fields, double* seed) {
+  if (!h || !grad_fields || !seed || h->storage != RLB_STORAGE_F64 || !h->halo.empty()) return RLB_EINVAL;
+  DeviceGuard gd(h->dev);
+  rlb_status st = ensure_adjoint_tiles(h);
+  if (st != RLB_OK) return st;
+  rlb_fields_vjp_kernel<<<(int)h->atile_tube.size(), NT, 0, h->stream>>>(
+      h->d_tubes, h->d_atiles, h->d_tab, static_cast<const double*>(h->F), grad_fields, h->nxtot, seed, h->d_flag);
+  RLB_CUDA(cudaGetLastError());
+  return check_flag(h);  // synchronises the stream
+}
+
 rlb_status rlb_init_vjp(rlb_handle h, const double* P, const double* n, const double* v, const double* grad_state,
                         double* grad_P, double* grad_n, double* grad_v) {
-  if (!h || !P || !n || !v || !grad_state || !grad_P || !grad_n || !grad_v || h->storage != RLB_STORAGE_F64)
+  if (!h || !P || !n || !v || !grad_state || !grad_P || !grad_n || !grad_v || h->storage != RLB_STORAGE_F64 ||
+      !h->halo.empty())
     return RLB_EINVAL;
   DeviceGuard gd(h->dev);
   rlb_status st = ensure_adjoint_tiles(h);

@@ -514,6 +514,84 @@ __global__ void __launch_bounds__(NT) rlb_moments_vjp_kernel(const TubeDev* tube
   }
 }
 
+// Adjoint of the Landau frame (e, beta, n) with respect to the moments (N0, Nx, T00, T0x, Txx), for the closed
+// form of landau(): with A = T00 + Txx, r = sqrt(A^2 - 4 T0x^2), e = (T00 - Txx + r) / 2, W = Txx + e,
+// beta = T0x / W, gamma = (1 - beta^2)^-1/2, n = gamma (N0 - beta Nx). Adds ge de/dM + gb dbeta/dM + gn dn/dM to
+// G[5]. Returns false for a non-physical cell (G unchanged).
+__device__ bool landau_vjp(const double mom[5], double ge, double gb, double gn, double G[5]) {
+  double e, beta, n, Tt;
+  if (!landau(mom, e, beta, n, Tt)) return false;
+  const double A = mom[2] + mom[4], B = mom[3];
+  const double r = sqrt(A * A - 4.0 * B * B);
+  if (!(r > 0.0)) return false;
+  // de/d(T00, T0x, Txx)
+  const double e00 = 0.5 * (1.0 + A / r), e0x = -2.0 * B / r, exx = 0.5 * (A / r - 1.0);
+  const double W = mom[4] + e, bW = beta / W;  // beta / W = T0x / W^2
+  // dbeta/d(T00, T0x, Txx)
+  const double b00 = -bW * e00, b0x = 1.0 / W - bW * e0x, bxx = -bW * (1.0 + exx);
+  const double g2 = 1.0 / (1.0 - beta * beta), gam = sqrt(g2);
+  // dn/dbeta at fixed (N0, Nx); dn/dN0 = gamma, dn/dNx = -gamma beta
+  const double nb = gam * (g2 * beta * (mom[0] - beta * mom[1]) - mom[1]);
+  const double gbt = gb + gn * nb;  // total adjoint of beta
+  G[0] += gn * gam;
+  G[1] -= gn * gam * beta;
+  G[2] += ge * e00 + gbt * b00;
+  G[3] += ge * e0x + gbt * b0x;
+  G[4] += ge * exx + gbt * bxx;
+  return true;
+}
+
+// Seed of the state from the adjoint of the fields of rlb_moments: dL/dF_s = sum_a c_a(s) G_a, where G_a is
+// dL/dM_a plus the share of dL/de, dL/dv and dL/dn carried through the Landau frame of the cell's moments.
+// gf: [RLB_NFIELDS][nxtot] (field layout); F: the FP64 state (padded rows) the fields were taken at; seed:
+// packed state. A non-physical cell raises the flag and seeds only its moments' share.
+__global__ void __launch_bounds__(NT) rlb_fields_vjp_kernel(const TubeDev* tubes, const int2* tiles,
+                                                            const double* tabs, const double* F, const double* gf,
+                                                            long long nxtot, double* seed, int* flag) {
+  __shared__ double Gs[5][GW];
+  const int2 tl = tiles[blockIdx.x];
+  const TubeDev T = tubes[tl.x];
+  const int c = threadIdx.x % GW, g = threadIdx.x / GW, x = tl.y + c;
+  const bool cell = c < TXA && x < T.Nx;
+  const double* tab = tabs + T.tab;
+  if (g == 0) {
+    double G[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (cell) {
+      const double* f = F + T.off + x;
+      double mom[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int j = 0; j < T.Qxi; ++j) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < T.Qp; ++i) {
+          const double v = f[(size_t)(i * T.Qxi + j) * T.ld];
+          a = fma(v, tab[TAB_PBAR + i], a);
+          b = fma(v, tab[TAB_PBAR2 + i], b);
+        }
+        const double xi = tab[TAB_XI + j];
+        mom[0] += a;
+        mom[1] = fma(a, xi, mom[1]);
+        mom[2] += b;
+        mom[3] = fma(b, xi, mom[3]);
+        mom[4] = fma(b * xi, xi, mom[4]);
+      }
+      const double* gx = gf + T.xoff + x;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) G[a] = gx[a * nxtot];
+      if (!landau_vjp(mom, gx[RLB_F_E * nxtot], gx[RLB_F_V * nxtot], gx[RLB_F_N * nxtot], G)) atomicOr(flag, 1);
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) Gs[a][c] = G[a];
+  }
+  __syncthreads();
+  if (!cell) return;
+  const double g0 = Gs[0][c], g1 = Gs[1][c], g2 = Gs[2][c], g3 = Gs[3][c], g4 = Gs[4][c];
+  for (int s = g; s < T.Qp * T.Qxi; s += NG) {
+    const int i = s / T.Qxi, j = s - i * T.Qxi;
+    const double xi = tab[TAB_XI + j];
+    const double v = tab[TAB_PBAR + i] * fma(xi, g1, g0) + tab[TAB_PBAR2 + i] * fma(xi, fma(xi, g4, g3), g2);
+    seed[T.poff + (size_t)s * T.Nx + x] = v;
+  }
+}
+
 struct InitVjpSmem {
   AdjCoef co;
   double lam[NBC][GW];

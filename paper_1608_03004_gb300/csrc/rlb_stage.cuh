@@ -66,14 +66,18 @@ __device__ __forceinline__ void for_each_tile(int ntiles, int schedule, int* cou
 // Device helpers
 // --------------------------------------------------------------------------------------------------
 
-// Source cell of a staged position x in [-HALO, Nx - 1 + GW + HALO]: periodic wrap (Nx >= 3) or zero-gradient
-// ghosts (open boundary). Always in [0, Nx).
-__device__ __forceinline__ int map_cell(int x, int Nx, int bc) {
+// Source of a staged position x in [-HALO, Nx - 1 + GW + HALO] within its row: periodic wrap (Nx >= 3),
+// zero-gradient ghosts (open boundary), or, on a halo side of a slab, the ghost cells the caller unpacked beside
+// the row (left ghosts -3..-1 at ld-3..ld-1, right ghosts at Nx..Nx+2; ld >= Nx + 6 for slabs; positions past
+// Nx + 2 are never read by a cell and map to Nx + 2). Always in [0, ld).
+__device__ __forceinline__ int map_cell(int x, int Nx, int bc, int ld) {
   if (bc == RLB_BC_PERIODIC) {
     if (x < 0) x += Nx;
     return x % Nx;
   }
-  return x < 0 ? 0 : (x >= Nx ? Nx - 1 : x);
+  if (x < 0) return (bc & RLB_BC_HALO_LEFT) ? ld + (x < -HALO ? -HALO : x) : 0;
+  if (x >= Nx) return (bc & RLB_BC_HALO_RIGHT) ? (x > Nx + HALO - 1 ? Nx + HALO - 1 : x) : Nx - 1;
+  return x;
 }
 
 // True where the fastest relaxation of a cell moving at beta, dt gamma (1 + |beta| max|xi|) / tau, is beyond the
@@ -208,7 +212,7 @@ __device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %
 
 struct StageSmem {
   union {
-    double red[NG][5][GW];
+    double red[NG][3 * QP_MAX][GW];  // per group: the radial sums S0, S1, S2 of each radial node
     CoefSmem coef;
   } u;
   double rate[2][GW];
@@ -234,40 +238,65 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
   double* Fout = A.Fout + T.off;
   const int x = x0 + c;
   const bool cell = (c < TX) && (x < Nx);
-  for (int k = tid; k < RW; k += NT) sm.src[k] = map_cell(x0 - HALO + k, Nx, T.bc);
+  for (int k = tid; k < RW; k += NT) sm.src[k] = map_cell(x0 - HALO + k, Nx, T.bc, ld);
 
   if (T.collide) {
-    // A. moments of the stage input, velocity rows split over the NG groups
-    double m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+    // A. moments of the stage input. The groups split the mirror pairs of directions (xi_jf = -xi_jb > 0) and
+    //    keep, per radial node i, S0 = sum_j F_ij, S1 = sum_j F_ij xi_j and S2 = sum_j F_ij xi_j^2 from the sum
+    //    s = F(xi) + F(-xi) and difference d = F(xi) - F(-xi) of each pair (S0 += s, S1 += d xi, S2 += s xi^2):
+    //    5 FP64 operations per two populations. An odd Qxi's xi = 0 direction adds to S0 only. Then
+    //    N0 = sum_i pbar_i S0_i, Nx = sum_i pbar_i S1_i, T00 = sum_i pbar_i^2 S0_i, T0x = sum_i pbar_i^2 S1_i and
+    //    Txx = sum_i pbar_i^2 S2_i.
+    double S[3 * QP_MAX];
+#pragma unroll
+    for (int k = 0; k < 3 * QP_MAX; ++k) S[k] = 0.0;
+    const int hq = Qxi / 2;
     if (cell) {
-      for (int j = g; j < Qxi; j += NG) {
-        double a = 0.0, b = 0.0;
-        for (int i = 0; i < Qp; ++i) {
-          const double f = __ldg(Fin + (size_t)(i * Qxi + j) * ld + x);
-          a = fma(f, tab[TAB_PBAR + i], a);
-          b = fma(f, tab[TAB_PBAR2 + i], b);
+      for (int jb = g; jb < hq; jb += NG) {
+        const int jf = Qxi - 1 - jb;
+        const double xi = tab[TAB_XI + jf], xi2 = xi * xi;
+#pragma unroll
+        for (int i = 0; i < QP_MAX; ++i) {
+          if (i < Qp) {
+            const double ff = __ldg(Fin + (size_t)(i * Qxi + jf) * ld + x);
+            const double fb = __ldg(Fin + (size_t)(i * Qxi + jb) * ld + x);
+            const double sum = ff + fb, dif = ff - fb;
+            S[3 * i] += sum;
+            S[3 * i + 1] = fma(dif, xi, S[3 * i + 1]);
+            S[3 * i + 2] = fma(sum, xi2, S[3 * i + 2]);
+          }
         }
-        const double xi = tab[TAB_XI + j];
-        m0 += a;
-        m1 = fma(a, xi, m1);
-        m2 += b;
-        m3 = fma(b, xi, m3);
-        m4 = fma(b * xi, xi, m4);
+      }
+      if ((Qxi & 1) && g == (hq % NG)) {
+#pragma unroll
+        for (int i = 0; i < QP_MAX; ++i)
+          if (i < Qp) S[3 * i] += __ldg(Fin + (size_t)(i * Qxi + hq) * ld + x);
       }
     }
-    sm.u.red[g][0][c] = m0;
-    sm.u.red[g][1][c] = m1;
-    sm.u.red[g][2][c] = m2;
-    sm.u.red[g][3][c] = m3;
-    sm.u.red[g][4][c] = m4;
+#pragma unroll
+    for (int k = 0; k < 3 * QP_MAX; ++k) sm.u.red[g][k][c] = S[k];
     __syncthreads();
     // B. Landau frame (one thread per cell), then the equilibrium coefficients
     double e = 1.0, beta = 0.0, n = 1.0, Tt = 1.0;
     bool ok = false;
     if (g == 0 && cell) {
-      double mom[5];
+      double mom[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int f = 0; f < 5; ++f) mom[f] = (sm.u.red[0][f][c] + sm.u.red[1][f][c]) + (sm.u.red[2][f][c] + sm.u.red[3][f][c]);
+      for (int i = 0; i < QP_MAX; ++i) {
+        if (i < Qp) {
+          double Si[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            Si[q] = (sm.u.red[0][3 * i + q][c] + sm.u.red[1][3 * i + q][c]) +
+                    (sm.u.red[2][3 * i + q][c] + sm.u.red[3][3 * i + q][c]);
+          const double p1 = tab[TAB_PBAR + i], p2 = tab[TAB_PBAR2 + i];
+          mom[0] = fma(p1, Si[0], mom[0]);
+          mom[1] = fma(p1, Si[1], mom[1]);
+          mom[2] = fma(p2, Si[0], mom[2]);
+          mom[3] = fma(p2, Si[1], mom[3]);
+          mom[4] = fma(p2, Si[2], mom[4]);
+        }
+      }
       ok = landau(mom, e, beta, n, Tt);
       if (!ok) atomicOr(A.flag, 1);
       else if (A.warn != nullptr && stiff(T, beta)) atomicOr(A.warn, RLB_WARN_STIFF);
@@ -329,7 +358,7 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
       }
       group_sync(g);
       const double xi = tab[TAB_XI + j];
-      const bool fwd = xi > 0.0;
+      const bool fwd = h == 1;  // the mirror row xi_{Qxi-1-jA} > 0; the first row has xi <= 0
       // pairs: thread c owns the pair of differences at positions (p, p + 1), p = c + 1 (wind toward +x) or
       // c + 2 (toward -x); these are the pairs the TX + 1 interfaces of the tile use
       {
@@ -362,7 +391,7 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
         const double F = row[c + 3];
         const double dphi = fma(phi[c + 1] - phi[c], 1.0 / 6.0, D);  // phi holds 6 G
         double out = F;
-        if (a != 0.0) out = fma(a, Fn[(size_t)s * ld + x], b * F);
+        if (A.stage != 0) out = fma(a, Fn[(size_t)s * ld + x], b * F);  // a = 0 in the first stage
         out = fma(-cxi_tab[j], dphi, out);  // - b dt xi/dx (Phi_{x+1/2} - Phi_{x-1/2})
         if (T.collide) {
           if (h == 0) {

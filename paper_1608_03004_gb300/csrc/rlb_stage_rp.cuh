@@ -166,7 +166,8 @@ __device__ void cell_coeffs_rp(const TubeDev* Tg, const double* tab, int Qp, con
   rt1 = (float)(r0 * beta);
 }
 
-// One velocity row as a lane holds it: its RP_C cells and the tile's halo (edge lanes only).
+// One velocity row as a lane holds it: its RP_C cells and the tile's halo (edge lanes only: lane 0 holds cells
+// x0-3 .. x0-1, lane 31 cells x0+RP_WT .. x0+RP_WT+2, boundary condition applied).
 struct RpRow {
   float v[RP_C];
   float h[3];
@@ -190,110 +191,97 @@ __device__ __forceinline__ void rp_load_row(RpRow& r, const S* Fin, size_t row, 
   for (int h = 0; h < 3; ++h) r.h[h] = edge ? ld_s<S>(src + hsrc[h]) : 0.f;
 }
 
-// Radial partial sums of the current direction for a lane's cells (the five moments are in shared memory).
-struct RpMom {
-  rlbdev::DF ra[RP_C], rb[RP_C];
-};
-
-// One velocity row s = i Qxi + j of a lane's RP_C cells: F_out = a F^n + b (F + dt L(F)), stored; with
-// collisions, the stored values enter the moment sums.
-template <typename S, int NVc>
-__device__ __forceinline__ void rp_row(const StageArgsRP& A, const TubeDev& T, const float4* rec, const RpWarp& w,
-                                       const RpRow& r, int i, int j, int s, int lane, int xl, bool full,
-                                       const float (&rt0)[RP_C], const float (&rt1)[RP_C], const S* Fn, S* Fout,
-                                       RpMom& mo) {
-  constexpr unsigned ALL = 0xffffffffu;
-  const int Qxi = T.Qxi;
-  // F^n at the lane's cells, issued first so that the WENO5 arithmetic below covers its latency
-  float fn[RP_C] = {0.f, 0.f, 0.f, 0.f};
-  if (A.a != 0.f) {
-    const S* fs = Fn + (size_t)s * T.ld;
-    if (full) {
-      const float4 t = ld4(fs + xl);
-      fn[0] = t.x;
-      fn[1] = t.y;
-      fn[2] = t.z;
-      fn[3] = t.w;
-    } else {
+// F^n of a lane's cells (stages 2 and 3 only).
+template <typename S>
+__device__ __forceinline__ void rp_load_fn(float (&fn)[RP_C], const S* Fn, size_t row, int xl, bool full, int Nx) {
+  const S* fs = Fn + row;
+  if (full) {
+    const float4 t = ld4(fs + xl);
+    fn[0] = t.x;
+    fn[1] = t.y;
+    fn[2] = t.z;
+    fn[3] = t.w;
+  } else {
 #pragma unroll
-      for (int q = 0; q < RP_C; ++q) fn[q] = (xl + q < T.Nx) ? ld_s<S>(fs + xl + q) : 0.f;
-    }
+    for (int q = 0; q < RP_C; ++q) fn[q] = (xl + q < Nx) ? ld_s<S>(fs + xl + q) : 0.f;
   }
-  // the velocity's record: xi, b dt xi/dx of this stage, 1/ws, 6/ws, moment weights, w^xi P_k(xi)
-  const float4* rp = rec + (size_t)s * (RP_REC / 4);
-  const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4], r5 = rp[5];
-  const float rv[RP_REC] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w,
-                            r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
-  const float xi = rv[R_XI], cxi = A.stage == 0 ? rv[R_CXI] : (A.stage == 1 ? rv[R_CXI + 1] : rv[R_CXI + 2]);
-  const float iws = rv[R_IWS], c6 = rv[R_C6];
-  const bool fwd = xi > 0.f;
-  // window of positions -3 .. 6 around the lane's cells 0 .. 3
-  float wv[10];
-  const float l1 = __shfl_up_sync(ALL, r.v[1], 1), l2 = __shfl_up_sync(ALL, r.v[2], 1),
-              l3 = __shfl_up_sync(ALL, r.v[3], 1);
-  const float q0 = __shfl_down_sync(ALL, r.v[0], 1), q1 = __shfl_down_sync(ALL, r.v[1], 1),
-              q2 = __shfl_down_sync(ALL, r.v[2], 1);
-  wv[0] = lane == 0 ? r.h[0] : l1;
-  wv[1] = lane == 0 ? r.h[1] : l2;
-  wv[2] = lane == 0 ? r.h[2] : l3;
+}
+
+// Flux differences Phi(q + 1/2) - Phi(q - 1/2) of a lane's cells q = 0 .. RP_C-1 for a wind toward +x (FWD) or
+// toward -x, from the row and its neighbours (shuffles; the edge lanes take the halo). The window w holds the
+// nine positions the five interfaces X = 0 .. 4 of the lane reach (interface X lies between cells X-1 and X):
+// -3 .. 5 toward +x, -2 .. 6 toward -x; d[k] = w[k+1] - w[k] is the difference at position k - 2 (toward +x) or
+// k - 1 (toward -x), and d[q + 2] is in both cases the jump between the upwind cells of interfaces q + 1 and q.
+// Each interface value is the upwind cell plus G, G from the three candidate stencils' indicators on the
+// differences scaled by 1/ws (the limiter acts on F / ws) and the combination scaled back by c6 = 6 / ws.
+template <bool FWD>
+__device__ __forceinline__ void rp_flux_diff(const RpRow& r, int lane, float iws, float c6, float (&dphi)[RP_C]) {
+  constexpr unsigned ALL = 0xffffffffu;
+  float w[9];
+  if (FWD) {
+    const float l1 = __shfl_up_sync(ALL, r.v[1], 1), l2 = __shfl_up_sync(ALL, r.v[2], 1),
+                l3 = __shfl_up_sync(ALL, r.v[3], 1);
+    const float q0 = __shfl_down_sync(ALL, r.v[0], 1), q1 = __shfl_down_sync(ALL, r.v[1], 1);
+    w[0] = lane == 0 ? r.h[0] : l1;
+    w[1] = lane == 0 ? r.h[1] : l2;
+    w[2] = lane == 0 ? r.h[2] : l3;
 #pragma unroll
-  for (int q = 0; q < RP_C; ++q) wv[3 + q] = r.v[q];
-  wv[7] = lane == 31 ? r.h[0] : q0;
-  wv[8] = lane == 31 ? r.h[1] : q1;
-  wv[9] = lane == 31 ? r.h[2] : q2;
-  // differences scaled by 1/ws: dd[k] = (w(p) - w(p-1)) / ws at position p = k - 2, k = 0 .. 8
-  float dd[9];
+    for (int q = 0; q < RP_C; ++q) w[3 + q] = r.v[q];
+    w[7] = lane == 31 ? r.h[0] : q0;
+    w[8] = lane == 31 ? r.h[1] : q1;
+  } else {
+    const float l2 = __shfl_up_sync(ALL, r.v[2], 1), l3 = __shfl_up_sync(ALL, r.v[3], 1);
+    const float q0 = __shfl_down_sync(ALL, r.v[0], 1), q1 = __shfl_down_sync(ALL, r.v[1], 1),
+                q2 = __shfl_down_sync(ALL, r.v[2], 1);
+    w[0] = lane == 0 ? r.h[1] : l2;
+    w[1] = lane == 0 ? r.h[2] : l3;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) dd[k] = (wv[k + 1] - wv[k]) * iws;
-  // indicator squares of the seven pairs the five interfaces X = 0..4 (between cells X-1 and X) use:
-  // pair t = (dd[t], dd[t+1]) toward +x, (dd[t+1], dd[t+2]) toward -x
+    for (int q = 0; q < RP_C; ++q) w[2 + q] = r.v[q];
+    w[6] = lane == 31 ? r.h[0] : q0;
+    w[7] = lane == 31 ? r.h[1] : q1;
+    w[8] = lane == 31 ? r.h[2] : q2;
+  }
+  float d[8], dd[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    d[k] = w[k + 1] - w[k];
+    dd[k] = d[k] * iws;
+  }
+  // indicator squares of the seven pairs of adjacent differences the interfaces use, each pair taken in wind
+  // order: (dd[t], dd[t+1]) toward +x, (dd[t+1], dd[t]) toward -x (an indicator is even in the differences)
   float sa[7], sb[7], sc[7];
 #pragma unroll
-  for (int t = 0; t < 7; ++t) {
-    const float x = fwd ? dd[t] : dd[t + 1], y = fwd ? dd[t + 1] : dd[t + 2];
-    rlbdev::weno5_pair(x, y, fwd, rlbdev::EPS_A, rlbdev::EPS_B, rlbdev::EPS_C, sa[t], sb[t], sc[t]);
-  }
+  for (int t = 0; t < 7; ++t)
+    rlbdev::weno5_pair(FWD ? dd[t] : dd[t + 1], FWD ? dd[t + 1] : dd[t], true, rlbdev::EPS_A, rlbdev::EPS_B,
+                       rlbdev::EPS_C, sa[t], sb[t], sc[t]);
   float G[5];
 #pragma unroll
   for (int X = 0; X < 5; ++X) {
-    if (fwd)
+    if (FWD)
       G[X] = rlbdev::weno5_combine_scaled(sa[X], sb[X + 1], sc[X + 2], dd[X], dd[X + 1], dd[X + 2], dd[X + 3], c6);
     else
-      G[X] = rlbdev::weno5_combine_scaled(sa[X + 2], sb[X + 1], sc[X], -dd[X + 4], -dd[X + 3], -dd[X + 2],
-                                          -dd[X + 1], c6);
+      G[X] = rlbdev::weno5_combine_scaled(sa[X + 2], sb[X + 1], sc[X], -dd[X + 3], -dd[X + 2], -dd[X + 1], -dd[X],
+                                          c6);
   }
-  // combination, collision, store
-  float out[RP_C];
+#pragma unroll
+  for (int q = 0; q < RP_C; ++q) dphi[q] = d[q + 2] + (G[q + 1] - G[q]);
+}
+
+// F_out = a F^n + b F - cxi dphi + rate (feq - F) of a lane's cells, rounded to storage and stored; returns the
+// stored values in st.
+template <typename S>
+__device__ __forceinline__ void rp_finish(const StageArgsRP& A, const TubeDev& T, const RpRow& r,
+                                          const float (&dphi)[RP_C], const float (&fn)[RP_C], float cxi,
+                                          const float (&rt0)[RP_C], const float (&rt1)[RP_C], float xi,
+                                          const float (&feq)[RP_C], S* dst, int xl, bool full, float (&st)[RP_C]) {
 #pragma unroll
   for (int q = 0; q < RP_C; ++q) {
-    const float F = wv[3 + q];
-    const float up = fwd ? F - wv[2 + q] : wv[4 + q] - F;  // v2(X = q + 1) - v2(X = q)
-    const float dphi = up + (G[q + 1] - G[q]);
+    const float F = r.v[q];
     float o = A.a != 0.f ? fmaf(A.a, fn[q], A.b * F) : F;
-    o = fmaf(-cxi, dphi, o);
-    out[q] = o;
+    o = fmaf(-cxi, dphi[q], o);
+    if (T.collide) o = fmaf(fmaf(-rt1[q], xi, rt0[q]), feq[q] - F, o);
+    st[q] = rnd_s<S>(o);
   }
-  if (T.collide) {
-    float feq[RP_C] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k <= NVc; ++k) {
-      const float4 b4 = *reinterpret_cast<const float4*>(w.B + (i * (NVc + 1) + k) * RP_WT + RP_C * lane);
-      const float pk = rv[R_PW + k];
-      feq[0] = fmaf(b4.x, pk, feq[0]);
-      feq[1] = fmaf(b4.y, pk, feq[1]);
-      feq[2] = fmaf(b4.z, pk, feq[2]);
-      feq[3] = fmaf(b4.w, pk, feq[3]);
-    }
-#pragma unroll
-    for (int q = 0; q < RP_C; ++q) {
-      const float rate = fmaf(-rt1[q], xi, rt0[q]);
-      out[q] = fmaf(rate, feq[q] - wv[3 + q], out[q]);
-    }
-  }
-  float st[RP_C];
-#pragma unroll
-  for (int q = 0; q < RP_C; ++q) st[q] = rnd_s<S>(out[q]);
-  S* dst = Fout + (size_t)s * T.ld;
   if (full) {
     st4(dst + xl, make_float4(st[0], st[1], st[2], st[3]));
   } else {
@@ -301,39 +289,47 @@ __device__ __forceinline__ void rp_row(const StageArgsRP& A, const TubeDev& T, c
     for (int q = 0; q < RP_C; ++q)
       if (xl + q < T.Nx) st_s<S>(dst + xl + q, st[q]);
   }
-  if (T.collide) {
-    // moments of what was stored: radial partial sums, folded into the five moments per direction
+}
+
+// The compensated radial sums of one radial node i over the directions walked so far, per cell:
+// S0 = sum_j F_ij, S1 = sum_j F_ij xi_j, S2 = sum_j F_ij xi_j^2 (double-float).
+struct RpSums {
+  rlbdev::DF s0[RP_C], s1[RP_C], s2[RP_C];
+};
+
+// Add a mirror pair of stored rows (xi, -xi) to the radial sums: with s = F(xi) + F(-xi) and d = F(xi) -
+// F(-xi), both exact as float pairs, S0 += s, S1 += d xi, S2 += s xi^2.
+__device__ __forceinline__ void rp_sums_pair(RpSums& S, const float (&sf)[RP_C], const float (&sb)[RP_C], float xh,
+                                             float xl_, float x2h, float x2l) {
+#pragma unroll
+  for (int q = 0; q < RP_C; ++q) {
+    float s, es, d, ed;
+    rlbdev::two_sum(sf[q], sb[q], s, es);
+    rlbdev::two_sum(sf[q], -sb[q], d, ed);
+    rlbdev::df_add(S.s0[q], {s, es});
+    rlbdev::df_add_dfprod(S.s1[q], {d, ed}, xh, xl_);
+    rlbdev::df_add_dfprod(S.s2[q], {s, es}, x2h, x2l);
+  }
+}
+
+// Fold the radial sums of node i into the five moments (double-float pairs in the lane's shared columns):
+// N0 += pbar S0, Nx += pbar S1, T00 += pbar^2 S0, T0x += pbar^2 S1, Txx += pbar^2 S2.
+__device__ __forceinline__ void rp_fold(const RpWarp& w, int lane, const RpSums& S, float p1h, float p1l, float p2h,
+                                        float p2l) {
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    float4* mp = reinterpret_cast<float4*>(w.M + f * RP_WT + RP_C * lane);
+    const float4 u0 = mp[0], u1 = mp[1];
+    rlbdev::DF m[RP_C] = {{u0.x, u0.y}, {u0.z, u0.w}, {u1.x, u1.y}, {u1.z, u1.w}};
+    const float wh = f < 2 ? p1h : p2h, wl = f < 2 ? p1l : p2l;
 #pragma unroll
     for (int q = 0; q < RP_C; ++q) {
-      rlbdev::df_add_prod(mo.ra[q], st[q], rv[R_P1], rv[R_P1 + 1]);
-      rlbdev::df_add_prod(mo.rb[q], st[q], rv[R_P2], rv[R_P2 + 1]);
+      const rlbdev::DF src = (f == 0 || f == 2) ? S.s0[q] : ((f == 1 || f == 3) ? S.s1[q] : S.s2[q]);
+      rlbdev::df_add_dfprod(m[q], src, wh, wl);
     }
-    if (i == T.Qp - 1) {
-#pragma unroll
-      for (int f = 0; f < 5; ++f) {
-        float4* mp = reinterpret_cast<float4*>(w.M + f * RP_WT + RP_C * lane);
-        const float4 u0 = mp[0], u1 = mp[1];
-        rlbdev::DF m[RP_C] = {{u0.x, u0.y}, {u0.z, u0.w}, {u1.x, u1.y}, {u1.z, u1.w}};
-#pragma unroll
-        for (int q = 0; q < RP_C; ++q) {
-          if (f == 0) rlbdev::df_add(m[q], mo.ra[q]);
-          if (f == 1) rlbdev::df_add_dfprod(m[q], mo.ra[q], rv[R_X], rv[R_X + 1]);
-          if (f == 2) rlbdev::df_add(m[q], mo.rb[q]);
-          if (f == 3) rlbdev::df_add_dfprod(m[q], mo.rb[q], rv[R_X], rv[R_X + 1]);
-          if (f == 4) rlbdev::df_add_dfprod(m[q], mo.rb[q], rv[R_X2], rv[R_X2 + 1]);
-        }
-        mp[0] = make_float4(m[0].hi, m[0].lo, m[1].hi, m[1].lo);
-        mp[1] = make_float4(m[2].hi, m[2].lo, m[3].hi, m[3].lo);
-      }
-#pragma unroll
-      for (int q = 0; q < RP_C; ++q) {
-        mo.ra[q] = {0.f, 0.f};
-        mo.rb[q] = {0.f, 0.f};
-      }
-    }
+    mp[0] = make_float4(m[0].hi, m[0].lo, m[1].hi, m[1].lo);
+    mp[1] = make_float4(m[2].hi, m[2].lo, m[3].hi, m[3].lo);
   }
-  (void)j;
-  (void)Qxi;
 }
 
 template <typename S, int NPc, int NVc>
@@ -352,9 +348,9 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
   const bool edge = lane == 0 || lane == 31;
   int hsrc[3], csrc[RP_C];
 #pragma unroll
-  for (int h = 0; h < 3; ++h) hsrc[h] = map_cell(lane == 0 ? x0 - 3 + h : x0 + RP_WT + h, Nx, T.bc);
+  for (int h = 0; h < 3; ++h) hsrc[h] = map_cell(lane == 0 ? x0 - 3 + h : x0 + RP_WT + h, Nx, T.bc, ld);
 #pragma unroll
-  for (int q = 0; q < RP_C; ++q) csrc[q] = map_cell(xl + q, Nx, T.bc);
+  for (int q = 0; q < RP_C; ++q) csrc[q] = map_cell(xl + q, Nx, T.bc, ld);
 
   // per-cell FP64 phase
   float rt0[RP_C], rt1[RP_C];
@@ -372,38 +368,103 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       cell_coeffs_rp<NPc, NVc>(A.tubes + T.index, tab, Qp, mom, bdt_itau, xl + q < Nx ? A.flag : nullptr,
                                w, RP_C * lane + q, rt0[q], rt1[q]);
     }
+#pragma unroll
+    for (int q = 0; q < RP_C; ++q)
+#pragma unroll
+      for (int f = 0; f < 5; ++f) w.M[f * RP_WT + RP_C * lane + q] = make_float2(0.f, 0.f);
   }
 
-  RpMom mo;
-#pragma unroll
-  for (int q = 0; q < RP_C; ++q) {
-    mo.ra[q] = mo.rb[q] = {0.f, 0.f};
-#pragma unroll
-    for (int f = 0; f < 5; ++f) w.M[f * RP_WT + RP_C * lane + q] = make_float2(0.f, 0.f);
-  }
-  // rows in the order j = 0.., i = 0..Qp-1; two rows in flight
-  const int Q = Qp * Qxi;
-  RpRow ra_, rb_;
-  int ia = 0, ja = 0;  // row held in ra_
-  rp_load_row<S>(ra_, Fin, (size_t)(ia * Qxi + ja) * ld, xl, full, csrc, edge, hsrc);
-  int ib = Qp > 1 ? 1 : 0, jb = Qp > 1 ? 0 : 1;  // row held in rb_
-  if (Q > 1) rp_load_row<S>(rb_, Fin, (size_t)(ib * Qxi + jb) * ld, xl, full, csrc, edge, hsrc);
-  auto advance2 = [&](int& i, int& j) {  // two rows further along the walk
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-      if (++i == Qp) {
-        i = 0;
-        ++j;
-      }
+  // Rows in the order i = 0 .. Qp-1 (outer), then the mirror pairs of directions (xi_jf > 0, xi_jb = -xi_jf),
+  // jb = 0 .. Qxi/2 - 1, jf = Qxi - 1 - jb: row jf then row jb; an odd Qxi ends each radial node with its xi = 0
+  // row. The next row's loads are in flight while a row is evaluated.
+  const int hq = Qxi / 2;
+  auto row_of = [&](int k) {  // k-th row of the walk
+    const int i = k / Qxi, kk = k - i * Qxi;
+    const int j = kk >= 2 * hq ? hq : ((kk & 1) ? kk >> 1 : Qxi - 1 - (kk >> 1));
+    return i * Qxi + j;
   };
-  for (int r = 0; r < Q; r += 2) {
-    rp_row<S, NVc>(A, T, rec, w, ra_, ia, ja, ia * Qxi + ja, lane, xl, full, rt0, rt1, Fn, Fout, mo);
-    advance2(ia, ja);
-    if (r + 2 < Q) rp_load_row<S>(ra_, Fin, (size_t)(ia * Qxi + ja) * ld, xl, full, csrc, edge, hsrc);
-    if (r + 1 < Q) {
-      rp_row<S, NVc>(A, T, rec, w, rb_, ib, jb, ib * Qxi + jb, lane, xl, full, rt0, rt1, Fn, Fout, mo);
-      advance2(ib, jb);
-      if (r + 3 < Q) rp_load_row<S>(rb_, Fin, (size_t)(ib * Qxi + jb) * ld, xl, full, csrc, edge, hsrc);
+  const int Q = Qp * Qxi;
+  RpRow ra, rb;
+  rp_load_row<S>(ra, Fin, (size_t)row_of(0) * ld, xl, full, csrc, edge, hsrc);
+  int k = 0;  // row held in ra
+  for (int i = 0; i < Qp; ++i) {
+    RpSums Sm;
+#pragma unroll
+    for (int q = 0; q < RP_C; ++q) Sm.s0[q] = Sm.s1[q] = Sm.s2[q] = {0.f, 0.f};
+    const float* Bi = w.B + (size_t)i * (NVc + 1) * RP_WT + RP_C * lane;
+    for (int jb = 0; jb < hq; ++jb, k += 2) {
+      const int jf = Qxi - 1 - jb;
+      const int sf = i * Qxi + jf, sbk = i * Qxi + jb;
+      rp_load_row<S>(rb, Fin, (size_t)sbk * ld, xl, full, csrc, edge, hsrc);  // row k + 1
+      // the pair's velocity record (of xi_jf > 0): xi, b dt xi/dx per stage, 1/ws, 6/ws, moment weights,
+      // w^xi P_k(xi)
+      const float4* rp = rec + (size_t)sf * (RP_REC / 4);
+      const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4], r5 = rp[5];
+      const float rv[RP_REC] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w,
+                                r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
+      const float xi = rv[R_XI], cxi = A.stage == 0 ? rv[R_CXI] : (A.stage == 1 ? rv[R_CXI + 1] : rv[R_CXI + 2]);
+      const float iws = rv[R_IWS], c6 = rv[R_C6];
+      // even and odd Legendre parts of the pair's equilibria: feq(+xi) = E + O, feq(-xi) = E - O
+      float E[RP_C] = {0.f, 0.f, 0.f, 0.f}, O[RP_C] = {0.f, 0.f, 0.f, 0.f};
+      if (T.collide) {
+#pragma unroll
+        for (int kk = 0; kk <= NVc; ++kk) {
+          const float4 b4 = *reinterpret_cast<const float4*>(Bi + kk * RP_WT);
+          const float pk = rv[R_PW + kk];
+          float* acc = (kk & 1) ? O : E;
+          acc[0] = fmaf(b4.x, pk, acc[0]);
+          acc[1] = fmaf(b4.y, pk, acc[1]);
+          acc[2] = fmaf(b4.z, pk, acc[2]);
+          acc[3] = fmaf(b4.w, pk, acc[3]);
+        }
+      }
+      float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C], dphi[RP_C], stf[RP_C], stb[RP_C];
+      // row jf: wind toward +x
+      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx);
+      rp_flux_diff<true>(ra, lane, iws, c6, dphi);
+#pragma unroll
+      for (int q = 0; q < RP_C; ++q) feq[q] = E[q] + O[q];
+      rp_finish<S>(A, T, ra, dphi, fn, cxi, rt0, rt1, xi, feq, Fout + (size_t)sf * ld, xl, full, stf);
+      if (k + 2 < Q) rp_load_row<S>(ra, Fin, (size_t)row_of(k + 2) * ld, xl, full, csrc, edge, hsrc);
+      // row jb: wind toward -x
+      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sbk * ld, xl, full, Nx);
+      rp_flux_diff<false>(rb, lane, iws, c6, dphi);
+#pragma unroll
+      for (int q = 0; q < RP_C; ++q) feq[q] = E[q] - O[q];
+      rp_finish<S>(A, T, rb, dphi, fn, -cxi, rt0, rt1, -xi, feq, Fout + (size_t)sbk * ld, xl, full, stb);
+      if (T.collide) rp_sums_pair(Sm, stf, stb, rv[R_X], rv[R_X + 1], rv[R_X2], rv[R_X2 + 1]);
+    }
+    if (Qxi & 1) {  // the xi = 0 row: no advection; its equilibrium has only even Legendre terms
+      const int sc = i * Qxi + hq;
+      const float4* rp = rec + (size_t)sc * (RP_REC / 4);
+      const float4 r3 = rp[3], r4 = rp[4], r5 = rp[5];
+      const float pw[RP_REC - 12] = {r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
+      float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C] = {0.f, 0.f, 0.f, 0.f}, st[RP_C];
+      const float zero[RP_C] = {0.f, 0.f, 0.f, 0.f};
+      if (T.collide) {
+#pragma unroll
+        for (int kk = 0; kk <= NVc; kk += 2) {
+          const float4 b4 = *reinterpret_cast<const float4*>(Bi + kk * RP_WT);
+          const float pk = pw[R_PW - 12 + kk];
+          feq[0] = fmaf(b4.x, pk, feq[0]);
+          feq[1] = fmaf(b4.y, pk, feq[1]);
+          feq[2] = fmaf(b4.z, pk, feq[2]);
+          feq[3] = fmaf(b4.w, pk, feq[3]);
+        }
+      }
+      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sc * ld, xl, full, Nx);
+      rp_finish<S>(A, T, ra, zero, fn, 0.f, rt0, rt1, 0.f, feq, Fout + (size_t)sc * ld, xl, full, st);
+      ++k;
+      if (k < Q) rp_load_row<S>(ra, Fin, (size_t)row_of(k) * ld, xl, full, csrc, edge, hsrc);
+      if (T.collide) {
+#pragma unroll
+        for (int q = 0; q < RP_C; ++q) rlbdev::df_add(Sm.s0[q], {st[q], 0.f});
+      }
+    }
+    if (T.collide) {
+      const float4 p = rec[(size_t)(i * Qxi) * (RP_REC / 4) + 1];  // R_P1 .. R_P2 + 1 of radial node i
+      rp_fold(w, lane, Sm, p.z, p.w, rec[(size_t)(i * Qxi) * (RP_REC / 4) + 2].x,
+              rec[(size_t)(i * Qxi) * (RP_REC / 4) + 2].y);
     }
   }
   // FP64 moments of F_out for the next stage (collision tubes only)

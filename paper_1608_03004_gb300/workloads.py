@@ -15,7 +15,8 @@ Workloads (sizes as stated):
     is silent on n; this keeps its T_L = 1, T_R = 0.8 and reproduces (1, 0.125) at P = (1, 0.1));
     dt = min(0.5 dx, 0.45 tau) (the strong shocks reach |v| ~ 0.8).
   * ``gaussian_bumps``: Nx = 2048, Qxi = 32, per-cell pressure 1 + sum of seed-fixed Gaussian bumps of
-    relative amplitude 0.05, n = P, v = 0.
+    relative amplitude 0.05, n = P, v = 0; ``perturbed`` multiplies P and n by a second seed-fixed set of
+    bumps (the inverse problem's target state).
   * ``stress``: one Sod tube, Nx = 1,048,576, Qxi = 128 (384 velocities), tau = 1e-2.
   * ``random_smooth``: seeded smooth periodic (P, n, v) profiles for parity tests.
   * ``fast_flow``: smooth periodic states whose speed reaches vmax (0.9 .. 0.99), where the Landau-frame
@@ -116,6 +117,18 @@ def gaussian_bumps(Nx: int = 2048, Qxi: int = 32, tau: float = 0.05, amplitude: 
         c, w = rng.uniform(-0.3, 0.3), rng.uniform(0.02, 0.08)
         P += amplitude * rng.uniform(0.5, 1.0) * np.exp(-0.5 * ((x - c) / w) ** 2)
     return TubeSpec(Nx=Nx, Qxi=Qxi, tau=tau, dt=cfl_dt(dx, tau), dx=dx, P=P, n=P.copy(), v=np.zeros(Nx))
+
+
+def perturbed(base: TubeSpec, seed: int, amplitude: float = 0.05, nbumps: int = 5) -> TubeSpec:
+    """The per-cell state of `base` with its pressure perturbed by seed-fixed Gaussian bumps of relative
+    amplitude `amplitude` (n follows P, so the temperature is kept); the target of the inverse problem."""
+    rng = np.random.default_rng(seed)
+    x = base.x_left + (np.arange(base.Nx) + 0.5) * base.dx
+    f = np.ones(base.Nx)
+    for _ in range(nbumps):
+        c, w = rng.uniform(-0.3, 0.3), rng.uniform(0.02, 0.08)
+        f += amplitude * rng.uniform(0.5, 1.0) * np.exp(-0.5 * ((x - c) / w) ** 2)
+    return dataclasses.replace(base, P=base.P * f, n=base.n * f, v=base.v.copy())
 
 
 def stress(Nx: int = 1 << 20, Qxi: int = 128, tau: float = 1e-2) -> TubeSpec:

@@ -5,6 +5,15 @@ Parity rule used by every GPU test: for each row r (one velocity of F, or one fi
 with scale_r = max_x |oracle_r| for F and for the positive fields, and the natural magnitude of the
 component for the fields that vanish at rest: max|N^0| for N^x, max|T^00| for T^0x, 1 (the speed of light)
 for v. The positive fields (N^0, T^00, T^xx, e, n) are also checked pointwise: |gpu - oracle| <= 10 rtol |oracle|.
+
+Ill-conditioned states (flows near |v| = 1) get a tolerance derived from their conditioning: two correct FP64
+evaluations that round differently differ by the rounding error times the condition number of the result.
+The condition number is measured with the oracle itself (``amplification``): the largest relative change of
+each output per unit relative perturbation of the initial populations (random, 1e-15). The Sod, rarefied and
+strong-shock cases measure A <= 10 (Sod 8.1, strong shock 7.2, rarefied 4.2) and keep the plain bar; the fast
+flows use rtol = 1e-12 max(1, A / 5): the bar scales with the amplification beyond 5 (|v| = 0.97: A = 110 for
+F, 394 for e; |v| = 0.99: 1.8e3 for F, 9.4e3 for e). The GPU-oracle gaps found there are about 0.4 (F at
+0.97), 0.1 (e at 0.99) and 0.005 (F, one step at 0.99 with a step too large) of that tolerance.
 """
 from __future__ import annotations
 
@@ -19,6 +28,7 @@ from paper_1608_03004_gb300.workloads import TubeSpec
 
 RTOL = 1e-12
 POSITIVE_FIELDS = (0, 2, 4, 5, 7)
+KAPPA_REF = 5.0  # amplification up to which the conditioned tolerance stays at the plain 1e-12 bar
 
 
 def to_tube(s: TubeSpec, storage: int = rb.STORAGE_F64) -> rb.Tube:
@@ -91,14 +101,42 @@ def field_errors(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
     return np.max(np.abs(gpu - ref), axis=1) / np.where(scale > 0, scale, 1.0)
 
 
-def assert_field_parity(gpu: np.ndarray, ref: np.ndarray, rtol: float = RTOL, what: str = "fields"):
+def assert_field_parity(gpu: np.ndarray, ref: np.ndarray, rtol=RTOL, what: str = "fields"):
+    """rtol: one tolerance for every field, or one per field."""
     e = field_errors(gpu, ref)
+    tol = np.broadcast_to(np.asarray(rtol, dtype=np.float64), e.shape)
     assert np.all(np.isfinite(gpu)), f"{what}: non-finite values"
-    assert e.max() <= rtol, f"{what}: worst field error {e.max():.3e} in field {rb.FIELDS[int(e.argmax())]}"
+    k = int(np.argmax(e / tol))
+    assert e[k] <= tol[k], f"{what}: worst field error {e[k]:.3e} in field {rb.FIELDS[k]} (tolerance {tol[k]:.3e})"
     for f in POSITIVE_FIELDS:
         pr = np.max(np.abs(gpu[f] - ref[f]) / np.abs(ref[f]))
-        assert pr <= 10 * rtol, f"{what}: pointwise error {pr:.3e} in {rb.FIELDS[f]}"
+        assert pr <= 10 * tol[f], f"{what}: pointwise error {pr:.3e} in {rb.FIELDS[f]}"
     return float(e.max())
+
+
+def amplification(s: TubeSpec, nsteps: int, delta: float = 1e-15, seeds: int = 3):
+    """Condition number of the oracle's run of `nsteps` steps from the initial state of s, measured: the largest
+    normwise change of F (over its rows) and of each field (in the parity rule's scales) per unit relative
+    perturbation of the initial populations, over `seeds` random perturbations of relative size delta.
+    Returns (A_F, A_fields[8])."""
+    p = to_params(s)
+    F0 = oracle_init(s)
+    Fa = oracle.step(p, F0, nsteps) if nsteps else F0
+    fa = oracle.fields(p, Fa)
+    aF, af = 0.0, np.zeros(len(rb.FIELDS))
+    for k in range(seeds):
+        r = np.random.default_rng(1000 + k).uniform(-1.0, 1.0, F0.shape)
+        Fp = F0 * (1.0 + delta * r)
+        Fb = oracle.step(p, Fp, nsteps) if nsteps else Fp
+        aF = max(aF, float(row_errors(Fb, Fa).max()) / delta)
+        af = np.maximum(af, field_errors(oracle.fields(p, Fb), fa) / delta)
+    return aF, af
+
+
+def conditioned_rtol(s: TubeSpec, nsteps: int):
+    """(rtol for F, rtol per field) = 1e-12 max(1, A / KAPPA_REF) with A from ``amplification``."""
+    aF, af = amplification(s, nsteps)
+    return RTOL * max(1.0, aF / KAPPA_REF), RTOL * np.maximum(1.0, af / KAPPA_REF)
 
 
 def oracle_run(s: TubeSpec, nsteps: int):
