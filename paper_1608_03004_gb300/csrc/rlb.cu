@@ -589,7 +589,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
         r[R_XI] = (float)xi[j];
         for (int st = 0; st < 3; ++st) r[R_CXI + st] = (float)T[tab_cxi(t.Qxi) + st * t.Qxi + j];
         r[R_IWS] = (float)iws;
-        r[R_C6] = (float)(6.0 * iws);
+        r[R_WS6] = (float)(1.0 / (6.0 * iws));
         split(pb[i], r + R_P1);
         split(pb[i] * pb[i], r + R_P2);
         split(xi[j], r + R_X);

@@ -17,6 +17,19 @@ __device__ __forceinline__ double rcp_nr(double d) {
 
 constexpr double WENO_EPS = 1e-6;
 
+// Products and sums that are rounded exactly as written. The compiler may contract a product into a following
+// addition (an FMA), and may do so differently in different inlined copies of the same expression. The
+// reduced-precision kernel evaluates each interface value and each indicator pair at a lane's edges twice (once
+// in each lane that uses it), and its compensated sums are error-free only if every addition is rounded as
+// written, so its FP32 arithmetic goes through these (mul.rn / add.rn / sub.rn are never contracted). The FP64
+// path evaluates every interface once and keeps the compiler's choices.
+__device__ __forceinline__ float mul_x(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_x(double a, double b) { return a * b; }
+__device__ __forceinline__ float add_x(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_x(double a, double b) { return a + b; }
+__device__ __forceinline__ float sub_x(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_x(double a, double b) { return a - b; }
+
 // Fifth-order WENO (Jiang & Shu) written on first differences d_l = v_l - v_{l-1} of five samples
 // v0..v4 ordered along the wind (v2 is the upwind cell next to the interface, whose value is v2 + G):
 //   candidates (2,-7,11)/6, (-1,5,2)/6, (2,5,-1)/6  =  v2 + r_k/6,  r0 = 5 d2 - 2 d1, r1 = d2 + 2 d3,
@@ -52,15 +65,15 @@ __device__ __forceinline__ float rcp_fast(float d) {
 // of its quadrature weight. T is double (FP64 path) or float (reduced-precision path).
 template <typename T>
 __device__ __forceinline__ void weno5_pair(T x, T y, bool fwd, T eA, T eB, T eC, T& sA, T& sB, T& sC) {
-  const T qx = x * x, pxy = x * y, qy = y * y;
+  const T qx = mul_x(x, x), pxy = mul_x(x, y), qy = mul_x(y, y);
   const T ax = fwd ? T(4.0 * C0) : T(10.0 * C0), ay = fwd ? T(10.0 * C0) : T(4.0 * C0);
   const T cx = fwd ? T(10.0 * C2) : T(4.0 * C2), cy = fwd ? T(4.0 * C2) : T(10.0 * C2);
   const T uA = fma(ax, qx, fma(T(-11.0 * C0), pxy, fma(ay, qy, eA)));
   const T uB = fma(T(4.0 * C1), qx, fma(T(-5.0 * C1), pxy, fma(T(4.0 * C1), qy, eB)));
   const T uC = fma(cx, qx, fma(T(-11.0 * C2), pxy, fma(cy, qy, eC)));
-  sA = uA * uA;
-  sB = uB * uB;
-  sC = uC * uC;
+  sA = mul_x(uA, uA);
+  sB = mul_x(uB, uB);
+  sC = mul_x(uC, uC);
 }
 
 // weno5_pair from the products x^2, x y, y^2 (the FP64 kernel forms each difference's square once and shares
@@ -81,28 +94,17 @@ __device__ __forceinline__ void weno5_pair_q(T qx, T pxy, T qy, bool fwd, T eA, 
 // d1..d4 in wind order (the FP64 stage kernel applies the 1/6 in the flux difference, where it costs nothing).
 template <typename T>
 __device__ __forceinline__ T weno5_combine6(T s0, T s1, T s2, T d1, T d2, T d3, T d4) {
-  const T r0 = fma(T(5.0), d2, T(-2.0) * d1), r1 = fma(T(2.0), d3, d2), r2 = fma(T(4.0), d3, -d4);
-  const T a0 = s1 * s2;
-  const T num = fma(s0, fma(s2, r1, s1 * r2), a0 * r0);
-  const T den = fma(s0, s1 + s2, a0);
-  return num * rcp_fast(den);
+  const T r0 = fma(T(5.0), d2, mul_x(T(-2.0), d1)), r1 = fma(T(2.0), d3, d2), r2 = fma(T(4.0), d3, -d4);
+  const T a0 = mul_x(s1, s2);
+  const T num = fma(s0, fma(s2, r1, mul_x(s1, r2)), mul_x(a0, r0));
+  const T den = fma(s0, add_x(s1, s2), a0);
+  return mul_x(num, rcp_fast(den));
 }
 
 // G of the interface.
 template <typename T>
 __device__ __forceinline__ T weno5_combine(T s0, T s1, T s2, T d1, T d2, T d3, T d4) {
   return weno5_combine6(s0, s1, s2, d1, d2, d3, d4) * T(1.0 / 6.0);
-}
-
-// weno5_combine for differences scaled by a common factor 1/ws (indicators of the weight-normalised values):
-// c6 = 6/ws in place of 6 returns G of the unscaled values (the weights do not depend on the scale).
-template <typename T>
-__device__ __forceinline__ T weno5_combine_scaled(T s0, T s1, T s2, T d1, T d2, T d3, T d4, T c6) {
-  const T r0 = fma(T(5.0), d2, T(-2.0) * d1), r1 = fma(T(2.0), d3, d2), r2 = fma(T(4.0), d3, -d4);
-  const T a0 = s1 * s2;
-  const T num = fma(s0, fma(s2, r1, s1 * r2), a0 * r0);
-  const T den = fma(s0, s1 + s2, a0);
-  return num * rcp_fast(c6 * den);
 }
 
 // Interface value v2 + G of five samples in memory order m0..m4 around the interface between m2 and m3
@@ -130,32 +132,32 @@ struct DF {
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 // acc += f (whi + wlo)
 __device__ __forceinline__ void df_add_prod(DF& acc, float f, float whi, float wlo) {
-  const float p = f * whi;
+  const float p = __fmul_rn(f, whi);
   float e = fmaf(f, whi, -p);
   e = fmaf(f, wlo, e);
   float s, t;
   two_sum(acc.hi, p, s, t);
   acc.hi = s;
-  acc.lo += t + e;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
 }
 
 // acc += a (xhi + xlo)
 __device__ __forceinline__ void df_add_dfprod(DF& acc, DF a, float xhi, float xlo) {
-  const float p = a.hi * xhi;
+  const float p = __fmul_rn(a.hi, xhi);
   float e = fmaf(a.hi, xhi, -p);
   e = fmaf(a.hi, xlo, e);
   e = fmaf(a.lo, xhi, e);
   float s, t;
   two_sum(acc.hi, p, s, t);
   acc.hi = s;
-  acc.lo += t + e;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
 }
 
 // acc += a
@@ -163,7 +165,7 @@ __device__ __forceinline__ void df_add(DF& acc, DF a) {
   float s, t;
   two_sum(acc.hi, a.hi, s, t);
   acc.hi = s;
-  acc.lo += t + a.lo;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, a.lo));
 }
 
 }  // namespace rlbdev

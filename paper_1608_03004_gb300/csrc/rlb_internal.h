@@ -70,12 +70,12 @@ inline int tab_size(int Qp, int Qxi) { return tab_eps(Qxi) + 3 * Qp * Qxi; }
 //   R_XI          xi_j
 //   R_CXI + st    b_st dt xi_j / dx for the three Runge-Kutta stages
 //   R_IWS         1 / ws, ws = w^p_i w^xi_j / 2 (the WENO5 limiter acts on F / ws)
-//   R_C6          6 / ws
+//   R_WS6         ws / 6
 //   R_P1, R_P2    pbar_i and pbar_i^2 as hi/lo float pairs (moment weights)
 //   R_X, R_X2     xi_j and xi_j^2 as hi/lo float pairs
 //   R_PW + k      w^xi_j P_k(xi_j), k <= NV_MAX (zero above Nv)
 constexpr int RP_REC = 24;
-constexpr int R_XI = 0, R_CXI = 1, R_IWS = 4, R_C6 = 5, R_P1 = 6, R_P2 = 8, R_X = 10, R_X2 = 12, R_PW = 14;
+constexpr int R_XI = 0, R_CXI = 1, R_IWS = 4, R_WS6 = 5, R_P1 = 6, R_P2 = 8, R_X = 10, R_X2 = 12, R_PW = 14;
 static_assert(R_PW + NV_MAX + 1 <= RP_REC, "record too small");
 inline int tabf_size(int Qp, int Qxi) { return Qp * Qxi * RP_REC; }
 

@@ -22,15 +22,42 @@
 // sums sum_i F pbar_i and sum_i F pbar_i^2 of one direction xi_j are folded into the five moments once per j.
 #pragma once
 
+// Loads of the streamed state rows bypass L1 (ld.global.nc.L1::no_allocate): every row is read once per stage,
+// and keeping it out of L1 leaves the little L1 that the shared-memory carveout spares to the per-velocity
+// records and tables that every warp reads again and again.
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned short ld_stream(const unsigned short* p) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream4(const float* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream2(const void* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+
 template <typename S>
 __device__ __forceinline__ float ld_s(const S* p);
 template <>
 __device__ __forceinline__ float ld_s<float>(const float* p) {
-  return __ldg(p);
+  return ld_stream(p);
 }
 template <>
 __device__ __forceinline__ float ld_s<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(__ldg(p));
+  const unsigned short u = ld_stream(reinterpret_cast<const unsigned short*>(p));
+  return __uint_as_float((unsigned)u << 16);
 }
 
 // The value a float becomes once stored as S.
@@ -47,9 +74,9 @@ __device__ __forceinline__ float rnd_s<__nv_bfloat16>(float v) {
 
 // Four consecutive stored values (16-byte aligned in FP32, 8-byte aligned in BF16) and their store; the
 // stored values are already representable in S.
-__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 ld4(const float* p) { return ld_stream4(p); }
 __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
-  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  const uint2 u = ld_stream2(p);
   const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
   const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
   return make_float4(a.x, a.y, b.x, b.y);
@@ -213,9 +240,10 @@ __device__ __forceinline__ void rp_load_fn(float (&fn)[RP_C], const S* Fn, size_
 // -3 .. 5 toward +x, -2 .. 6 toward -x; d[k] = w[k+1] - w[k] is the difference at position k - 2 (toward +x) or
 // k - 1 (toward -x), and d[q + 2] is in both cases the jump between the upwind cells of interfaces q + 1 and q.
 // Each interface value is the upwind cell plus G, G from the three candidate stencils' indicators on the
-// differences scaled by 1/ws (the limiter acts on F / ws) and the combination scaled back by c6 = 6 / ws.
+// differences scaled by 1/ws (the limiter acts on F / ws): the combination of the scaled differences returns
+// 6 G / ws, and the flux difference scales it back with ws6 = ws / 6 in its one FMA.
 template <bool FWD>
-__device__ __forceinline__ void rp_flux_diff(const RpRow& r, int lane, float iws, float c6, float (&dphi)[RP_C]) {
+__device__ __forceinline__ void rp_flux_diff(const RpRow& r, int lane, float iws, float ws6, float (&dphi)[RP_C]) {
   constexpr unsigned ALL = 0xffffffffu;
   float w[9];
   if (FWD) {
@@ -244,8 +272,8 @@ __device__ __forceinline__ void rp_flux_diff(const RpRow& r, int lane, float iws
   float d[8], dd[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    d[k] = w[k + 1] - w[k];
-    dd[k] = d[k] * iws;
+    d[k] = __fsub_rn(w[k + 1], w[k]);
+    dd[k] = __fmul_rn(d[k], iws);
   }
   // indicator squares of the seven pairs of adjacent differences the interfaces use, each pair taken in wind
   // order: (dd[t], dd[t+1]) toward +x, (dd[t+1], dd[t]) toward -x (an indicator is even in the differences)
@@ -254,17 +282,16 @@ __device__ __forceinline__ void rp_flux_diff(const RpRow& r, int lane, float iws
   for (int t = 0; t < 7; ++t)
     rlbdev::weno5_pair(FWD ? dd[t] : dd[t + 1], FWD ? dd[t + 1] : dd[t], true, rlbdev::EPS_A, rlbdev::EPS_B,
                        rlbdev::EPS_C, sa[t], sb[t], sc[t]);
-  float G[5];
+  float G6[5];  // 6 G / ws of each interface
 #pragma unroll
   for (int X = 0; X < 5; ++X) {
     if (FWD)
-      G[X] = rlbdev::weno5_combine_scaled(sa[X], sb[X + 1], sc[X + 2], dd[X], dd[X + 1], dd[X + 2], dd[X + 3], c6);
+      G6[X] = rlbdev::weno5_combine6(sa[X], sb[X + 1], sc[X + 2], dd[X], dd[X + 1], dd[X + 2], dd[X + 3]);
     else
-      G[X] = rlbdev::weno5_combine_scaled(sa[X + 2], sb[X + 1], sc[X], -dd[X + 3], -dd[X + 2], -dd[X + 1], -dd[X],
-                                          c6);
+      G6[X] = rlbdev::weno5_combine6(sa[X + 2], sb[X + 1], sc[X], -dd[X + 3], -dd[X + 2], -dd[X + 1], -dd[X]);
   }
 #pragma unroll
-  for (int q = 0; q < RP_C; ++q) dphi[q] = d[q + 2] + (G[q + 1] - G[q]);
+  for (int q = 0; q < RP_C; ++q) dphi[q] = fmaf(__fsub_rn(G6[q + 1], G6[q]), ws6, d[q + 2]);
 }
 
 // F_out = a F^n + b F - cxi dphi + rate (feq - F) of a lane's cells, rounded to storage and stored; returns the
@@ -277,9 +304,9 @@ __device__ __forceinline__ void rp_finish(const StageArgsRP& A, const TubeDev& T
 #pragma unroll
   for (int q = 0; q < RP_C; ++q) {
     const float F = r.v[q];
-    float o = A.a != 0.f ? fmaf(A.a, fn[q], A.b * F) : F;
+    float o = A.a != 0.f ? fmaf(A.a, fn[q], __fmul_rn(A.b, F)) : F;
     o = fmaf(-cxi, dphi[q], o);
-    if (T.collide) o = fmaf(fmaf(-rt1[q], xi, rt0[q]), feq[q] - F, o);
+    if (T.collide) o = fmaf(fmaf(-rt1[q], xi, rt0[q]), __fsub_rn(feq[q], F), o);
     st[q] = rnd_s<S>(o);
   }
   if (full) {
@@ -396,14 +423,14 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       const int jf = Qxi - 1 - jb;
       const int sf = i * Qxi + jf, sbk = i * Qxi + jb;
       rp_load_row<S>(rb, Fin, (size_t)sbk * ld, xl, full, csrc, edge, hsrc);  // row k + 1
-      // the pair's velocity record (of xi_jf > 0): xi, b dt xi/dx per stage, 1/ws, 6/ws, moment weights,
+      // the pair's velocity record (of xi_jf > 0): xi, b dt xi/dx per stage, 1/ws, ws/6, moment weights,
       // w^xi P_k(xi)
       const float4* rp = rec + (size_t)sf * (RP_REC / 4);
       const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4], r5 = rp[5];
       const float rv[RP_REC] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w,
                                 r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
       const float xi = rv[R_XI], cxi = A.stage == 0 ? rv[R_CXI] : (A.stage == 1 ? rv[R_CXI + 1] : rv[R_CXI + 2]);
-      const float iws = rv[R_IWS], c6 = rv[R_C6];
+      const float iws = rv[R_IWS], ws6 = rv[R_WS6];
       // even and odd Legendre parts of the pair's equilibria: feq(+xi) = E + O, feq(-xi) = E - O
       float E[RP_C] = {0.f, 0.f, 0.f, 0.f}, O[RP_C] = {0.f, 0.f, 0.f, 0.f};
       if (T.collide) {
@@ -421,16 +448,16 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C], dphi[RP_C], stf[RP_C], stb[RP_C];
       // row jf: wind toward +x
       if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx);
-      rp_flux_diff<true>(ra, lane, iws, c6, dphi);
+      rp_flux_diff<true>(ra, lane, iws, ws6, dphi);
 #pragma unroll
-      for (int q = 0; q < RP_C; ++q) feq[q] = E[q] + O[q];
+      for (int q = 0; q < RP_C; ++q) feq[q] = __fadd_rn(E[q], O[q]);
       rp_finish<S>(A, T, ra, dphi, fn, cxi, rt0, rt1, xi, feq, Fout + (size_t)sf * ld, xl, full, stf);
       if (k + 2 < Q) rp_load_row<S>(ra, Fin, (size_t)row_of(k + 2) * ld, xl, full, csrc, edge, hsrc);
       // row jb: wind toward -x
       if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sbk * ld, xl, full, Nx);
-      rp_flux_diff<false>(rb, lane, iws, c6, dphi);
+      rp_flux_diff<false>(rb, lane, iws, ws6, dphi);
 #pragma unroll
-      for (int q = 0; q < RP_C; ++q) feq[q] = E[q] - O[q];
+      for (int q = 0; q < RP_C; ++q) feq[q] = __fsub_rn(E[q], O[q]);
       rp_finish<S>(A, T, rb, dphi, fn, -cxi, rt0, rt1, -xi, feq, Fout + (size_t)sbk * ld, xl, full, stb);
       if (T.collide) rp_sums_pair(Sm, stf, stb, rv[R_X], rv[R_X + 1], rv[R_X2], rv[R_X2 + 1]);
     }
