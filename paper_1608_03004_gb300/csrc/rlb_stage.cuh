@@ -87,15 +87,25 @@ __device__ __forceinline__ bool stiff(const TubeDev& T, double beta) {
   return k * k > T.stiff_lim * T.stiff_lim * (1.0 - beta * beta);      // (k gamma)^2 > stiff_lim^2, no square root
 }
 
-// Landau frame from (N0, Nx, T00, T0x, Txx): e, beta, n (Landau), T. Returns false if non-physical.
-__device__ __forceinline__ bool landau(const double mom[5], double& e, double& beta, double& n, double& T) {
+// Landau frame from (N0, Nx, T00, T0x, Txx): e, beta, n (Landau), T, and gamma = (1 - beta^2)^-1/2 if gam_out is
+// given. Returns false if non-physical. A cell at rest (T0x = 0, exactly so wherever the state is symmetric in xi)
+// skips the division and square root that give beta = 0, gamma = 1 and n = N0.
+__device__ __forceinline__ bool landau(const double mom[5], double& e, double& beta, double& n, double& T,
+                                       double* gam_out = nullptr) {
   const double A = mom[2] + mom[4];
   const double disc = A * A - 4.0 * mom[3] * mom[3];
   e = 0.5 * ((mom[2] - mom[4]) + sqrt(disc));
-  beta = mom[3] / (mom[4] + e);
-  const double gam = 1.0 / sqrt(1.0 - beta * beta);
-  n = gam * (mom[0] - beta * mom[1]);
+  double gam = 1.0;
+  if (mom[3] == 0.0) {
+    beta = 0.0;
+    n = mom[0];
+  } else {
+    beta = mom[3] / (mom[4] + e);
+    gam = 1.0 / sqrt(1.0 - beta * beta);
+    n = gam * (mom[0] - beta * mom[1]);
+  }
   T = e / (3.0 * n);
+  if (gam_out) *gam_out = gam;
   return disc >= 0.0 && e > 0.0 && fabs(beta) < 1.0 && n > 0.0 && T > 0.0;
 }
 

@@ -148,25 +148,44 @@ __host__ __device__ inline int rp_brows(int Qp, int Np, int Nv) { return Qp * ((
 template <int NPc, int NVc>
 __device__ void cell_coeffs_rp(const TubeDev* Tg, const double* tab, int Qp, const double mom[5], double bdt_itau,
                                int* flag, const RpWarp& w, int col, float& rt0, float& rt1) {
-  double e, beta, n, Tt;
-  bool ok = landau(mom, e, beta, n, Tt);
+  double e, beta, n, Tt, gam;
+  bool ok = landau(mom, e, beta, n, Tt, &gam);
   // flag[1] holds the sticky warning bits (RLB_WARN_*); the tube record is read from global memory here
   if (ok && flag != nullptr && stiff(*Tg, beta)) atomicOr(flag + 1, RLB_WARN_STIFF);
+  if (ok && beta == 0.0) {
+    // at rest hhat_{m,k} = delta_{k0}: only B[i][0] = n/(4T^3) w^p_i sum_q T^(q+2) K[i][q] is nonzero (the same
+    // FP64 operations as the general path below takes at beta = 0)
+    const double pref = n / (4.0 * Tt * Tt * Tt);
+#pragma unroll
+    for (int i = 0; i < QP_MAX; ++i) {
+      if (i < Qp) {
+        const double pw = pref * tab[TAB_WP + i];
+        double B0 = 0.0, sq = Tt * Tt;
+#pragma unroll
+        for (int q = 0; q <= NPc; ++q) {
+          const double G = pw * sq * tab[TAB_K + i * (NP_MAX + 1) + q];
+          B0 = fma(G, 1.0, B0);
+          sq *= Tt;
+        }
+        w.B[(i * (NVc + 1)) * RP_WT + col] = (float)B0;
+#pragma unroll
+        for (int k = 1; k <= NVc; ++k) w.B[(i * (NVc + 1) + k) * RP_WT + col] = 0.f;
+      }
+    }
+    rt0 = (float)bdt_itau;
+    rt1 = 0.f;
+    return;
+  }
   double hh[(NPc + 1) * (NV_MAX + 1)];
 #pragma unroll
   for (int k = 0; k < (NPc + 1) * (NV_MAX + 1); ++k) hh[k] = 0.0;
   if (ok) {
-    if (beta == 0.0) {
-#pragma unroll
-      for (int m = 0; m <= NPc; ++m) hh[m * (NV_MAX + 1)] = 1.0;
-    } else {
-      const bool c0 = hhat_parity<NPc, NVc, 0, 1>(beta, hh);
-      const bool c1 = hhat_parity<NPc, NVc, 1, 1>(beta, hh);
-      ok = c0 && c1;
-    }
+    const bool c0 = hhat_parity<NPc, NVc, 0, 1>(beta, hh);
+    const bool c1 = hhat_parity<NPc, NVc, 1, 1>(beta, hh);
+    ok = c0 && c1;
   }
   if (!ok && flag) atomicOr(flag, 1);
-  const double s = ok ? Tt * sqrt(1.0 - beta * beta) : 0.0;
+  const double s = ok ? Tt / gam : 0.0;
 #pragma unroll
   for (int i = 0; i < QP_MAX; ++i) {
     double B[NVc + 1];
@@ -188,7 +207,7 @@ __device__ void cell_coeffs_rp(const TubeDev* Tg, const double* tab, int Qp, con
       for (int k = 0; k <= NVc; ++k) w.B[(i * (NVc + 1) + k) * RP_WT + col] = (float)B[k];
     }
   }
-  const double r0 = ok ? bdt_itau / sqrt(1.0 - beta * beta) : 0.0;
+  const double r0 = ok ? bdt_itau * gam : 0.0;
   rt0 = (float)r0;
   rt1 = (float)(r0 * beta);
 }
