@@ -433,6 +433,9 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
   RpRow ra, rb;
   rp_load_row<S>(ra, Fin, (size_t)row_of(0) * ld, xl, full, csrc, edge, hsrc);
   int k = 0;  // row held in ra
+  // The record's second float4 (1/ws, ws/6), which the first row of a pair needs at once, is loaded one pair
+  // ahead; the rest of the record is needed only after that row's flux differences, which cover its latency.
+  float4 nr1 = rec[(size_t)(Qxi - 1) * (RP_REC / 4) + 1];
   for (int i = 0; i < Qp; ++i) {
     RpSums Sm;
 #pragma unroll
@@ -445,11 +448,20 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       // the pair's velocity record (of xi_jf > 0): xi, b dt xi/dx per stage, 1/ws, ws/6, moment weights,
       // w^xi P_k(xi)
       const float4* rp = rec + (size_t)sf * (RP_REC / 4);
-      const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3], r4 = rp[4], r5 = rp[5];
+      const float4 r1 = nr1;
+      {
+        const int sn = jb + 1 < hq ? sf - 1 : (i + 1 < Qp ? (i + 1) * Qxi + Qxi - 1 : sf);
+        nr1 = rec[(size_t)sn * (RP_REC / 4) + 1];
+      }
+      const float4 r0 = rp[0], r2 = rp[2], r3 = rp[3], r4 = rp[4], r5 = rp[5];
       const float rv[RP_REC] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w,
                                 r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
       const float xi = rv[R_XI], cxi = A.stage == 0 ? rv[R_CXI] : (A.stage == 1 ? rv[R_CXI + 1] : rv[R_CXI + 2]);
       const float iws = rv[R_IWS], ws6 = rv[R_WS6];
+      float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C], dphi[RP_C], stf[RP_C], stb[RP_C];
+      // row jf: wind toward +x
+      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx);
+      rp_flux_diff<true>(ra, lane, iws, ws6, dphi);
       // even and odd Legendre parts of the pair's equilibria: feq(+xi) = E + O, feq(-xi) = E - O
       float E[RP_C] = {0.f, 0.f, 0.f, 0.f}, O[RP_C] = {0.f, 0.f, 0.f, 0.f};
       if (T.collide) {
@@ -464,10 +476,6 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
           acc[3] = fmaf(b4.w, pk, acc[3]);
         }
       }
-      float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C], dphi[RP_C], stf[RP_C], stb[RP_C];
-      // row jf: wind toward +x
-      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx);
-      rp_flux_diff<true>(ra, lane, iws, ws6, dphi);
 #pragma unroll
       for (int q = 0; q < RP_C; ++q) feq[q] = __fadd_rn(E[q], O[q]);
       rp_finish<S>(A, T, ra, dphi, fn, cxi, rt0, rt1, xi, feq, Fout + (size_t)sf * ld, xl, full, stf);
