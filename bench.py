@@ -61,16 +61,19 @@ FLOPS_PER_NODE_STAGE = 84
 # Algorithmic HBM bytes per velocity node per step with one launch per stage: stage inputs read once
 # (1 + 2 + 2 doubles), outputs written once (3 doubles).
 BYTES_PER_NODE_STEP = 64
-PROFILES = {"adjoint": os.path.join(ROOT, "profiles", "rlb_adjoint_kernel_gradient.md"),
-            "f64": os.path.join(ROOT, "profiles", "rlb_stage_kernel_sod_sweep.md"),
-            "f32": os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_f32_stress.md"),
-            "bf16": os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_bf16_stress.md")}
+# ncu summaries by (kernel kind, workload): bench.py reports a kernel's DRAM traffic per launch only from the summary
+# taken on that workload while the kernel's sources still hash to the recorded value
+PROFILES = {("adjoint", "gradient"): os.path.join(ROOT, "profiles", "rlb_adjoint_kernel_gradient.md"),
+            ("f64", "stress"): os.path.join(ROOT, "profiles", "rlb_stage_kernel_stress.md"),
+            ("f64", "sweep"): os.path.join(ROOT, "profiles", "rlb_stage_kernel_sod_sweep.md"),
+            ("f32", "stress"): os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_f32_stress.md"),
+            ("bf16", "stress"): os.path.join(ROOT, "profiles", "rlb_stage_rp_kernel_bf16_stress.md")}
 _CSRC = os.path.join(ROOT, "paper_1608_03004_gb300", "csrc")
 _SHARED = [os.path.join(_CSRC, "rlb_device_math.cuh"), os.path.join(_CSRC, "rlb_internal.h")]
-KERNEL_SRCS = {"adjoint": [os.path.join(_CSRC, "rlb_adjoint.cuh")] + _SHARED,
+KERNEL_SRCS = {"adjoint": [os.path.join(_CSRC, "rlb_adjoint.cuh"), os.path.join(_CSRC, "rlb_stage.cuh")] + _SHARED,
                "f64": [os.path.join(_CSRC, "rlb_stage.cuh")] + _SHARED,
-               "f32": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED,
-               "bf16": [os.path.join(_CSRC, "rlb_stage_rp.cuh")] + _SHARED}
+               "f32": [os.path.join(_CSRC, "rlb_stage_rp.cuh"), os.path.join(_CSRC, "rlb_stage.cuh")] + _SHARED,
+               "bf16": [os.path.join(_CSRC, "rlb_stage_rp.cuh"), os.path.join(_CSRC, "rlb_stage.cuh")] + _SHARED}
 ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
 EXTRA_STEPS = 40  # timed steps of each extra configuration (after the headline's warm-up count)
 CPU_SAMPLE_NODES = 24_000_000  # bound on the velocity nodes the oracle advances per CPU sample step
@@ -324,22 +327,27 @@ def measured_peaks() -> dict:
         return {}
 
 
-def ncu_traffic_per_launch(precision: str, workload: str):
-    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on the current kernel and on
-    this workload."""
+def kernel_sources_sha(kind: str) -> str:
+    """First 16 hex digits of the sha256 of a kernel's sources (the value the ncu summaries record)."""
+    h = hashlib.sha256()
+    for src in KERNEL_SRCS[kind]:
+        h.update(open(src, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_launch(kind: str, workload: str):
+    """DRAM bytes per stage launch from the committed ncu summary of this kernel on this workload, if it was taken
+    on the current kernel sources."""
+    path = PROFILES.get((kind, workload))
     try:
-        text = open(PROFILES[precision]).read()
+        text = open(path).read() if path else None
     except OSError:
         return None
-    if f"workload: {workload}" not in text:  # the profile names the workload it was captured on
+    if text is None or f"workload: {workload}" not in text:
         return None
-    h = hashlib.sha256()
-    for src in KERNEL_SRCS[precision]:
-        h.update(open(src, "rb").read())
-    sha = h.hexdigest()[:16]
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"dram_bytes_per_stage_launch_full_size:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_tr or m_sha.group(1) != sha:
+    if not m_sha or not m_tr or m_sha.group(1) != kernel_sources_sha(kind):
         return None
     return float(m_tr.group(1))
 
