@@ -758,7 +758,7 @@ def run_gradient(args, specs, desc, rank, world, emit=True):
                              "DFMA/clk x 2 flops x max SM clock (derived)"},
         "e2e": {"value": whole_job_rate(nodes, GRAD_STEPS * e2e_steps, world, e2e_s), "unit": GRAD_UNIT,
                 "h2d_bytes_per_step": 3 * 8 * h.nx_total, "d2h_bytes_per_step": 3 * 8 * h.nx_total + 8 * len(tubes),
-                "steps": e2e_steps, "api": "adjoint.run_moments (torch.autograd) from pinned host fields, "
+                "steps": e2e_steps, "api": "adjoint.run_fields (torch.autograd) from pinned host fields, "
                                           "gradients read back"},
         "clocks": clk,
         "gpu_launches": 9 * GRAD_STEPS + 3,
