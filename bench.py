@@ -343,7 +343,8 @@ def ncu_traffic_per_launch(kind: str, workload: str):
         text = open(path).read() if path else None
     except OSError:
         return None
-    if text is None or f"workload: {workload}" not in text:
+    m_wl = re.search(r"^\s*workload:\s*(\S+)", text or "", re.M)
+    if not m_wl or m_wl.group(1) != workload:
         return None
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"dram_bytes_per_stage_launch_full_size:\s*([0-9.eE+]+)", text)
