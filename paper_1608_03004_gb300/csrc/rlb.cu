@@ -425,9 +425,10 @@ void free_ctx(rlb_ctx* h) {
   delete h;
 }
 
-// WENO5 epsilon terms of every velocity: 3 eps ws^2 (C0, C1, C2), ws = w^p_i w^xi_j / 2 (the limiter acts on
-// the weight-normalised population F_s / ws with eps = 1e-6).
-void fill_eps(double* out, int Qp, int Qxi, const double* wp, const double* wxi) {
+// WENO5 epsilon terms of every velocity: 3 eps ws^2 (C0, C1, C2) into out, ws = w^p_i w^xi_j / 2 (the limiter
+// acts on the weight-normalised population F_s / ws with eps = 1e-6), and e = 3 eps ws^2 as the float pair
+// (hi, lo), hi + lo = e to about 48 bits, into the 8 bytes of outf[s].
+void fill_eps(double* out, double* outf, int Qp, int Qxi, const double* wp, const double* wxi) {
   for (int i = 0; i < Qp; ++i)
     for (int j = 0; j < Qxi; ++j) {
       const double ws = 0.5 * wp[i] * wxi[j];
@@ -436,6 +437,8 @@ void fill_eps(double* out, int Qp, int Qxi, const double* wp, const double* wxi)
       o[0] = e * rlbdev::C0;
       o[1] = e * rlbdev::C1;
       o[2] = e * rlbdev::C2;
+      const float pair[2] = {(float)e, (float)(e - (double)(float)e)};
+      std::memcpy(outf + i * Qxi + j, pair, sizeof(pair));
     }
 }
 
@@ -465,7 +468,7 @@ bool fill_tube_tables(const rlb_tube& t, double* pb, double* wp, double* xi, dou
       T[tab_pw(t.Qxi) + j * (NV_MAX + 1) + k] = k <= t.Nv ? wxi[j] * rlbq::legendre(k, xi[j]) : 0.0;
     for (int st = 0; st < 3; ++st) T[tab_cxi(t.Qxi) + st * t.Qxi + j] = RK_B[st] * t.dt * xi[j] / t.dx;
   }
-  fill_eps(T + tab_eps(t.Qxi), t.Qp, t.Qxi, wp, wxi);
+  fill_eps(T + tab_eps(t.Qxi), T + tab_epsf(t.Qp, t.Qxi), t.Qp, t.Qxi, wp, wxi);
   return true;
 }
 

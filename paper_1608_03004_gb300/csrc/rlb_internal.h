@@ -55,7 +55,9 @@ struct TubeDev {
 //   then xi_j (Qxi), then w^xi_j P_k(xi_j) at [j (NV_MAX+1) + k] (Qxi (NV_MAX+1)), zero for k > Nv,
 //   then b_st dt xi_j / dx at [st Qxi + j] for the three Runge-Kutta stages, b = (1, 1/4, 2/3),
 //   then per velocity s = i Qxi + j the WENO5 epsilon terms 3 eps ws^2 (C0, C1, C2) at [3 s + 0..2],
-//   ws = w^p_i w^xi_j / 2 (the limiter acts on the weight-normalised population)
+//   ws = w^p_i w^xi_j / 2 (the limiter acts on the weight-normalised population),
+//   then per velocity s the term e = 3 eps ws^2 as a float pair (hi, lo) in the 8 bytes of slot s (the FP64
+//   stage kernel's double-float limiter)
 constexpr int TAB_PBAR = 0;
 constexpr int TAB_PBAR2 = QP_MAX;
 constexpr int TAB_WP = 2 * QP_MAX;
@@ -64,7 +66,8 @@ constexpr int TAB_XI = TAB_K + QP_MAX * (NP_MAX + 1);
 __host__ __device__ inline int tab_pw(int Qxi) { return TAB_XI + Qxi; }
 __host__ __device__ inline int tab_cxi(int Qxi) { return TAB_XI + Qxi + Qxi * (NV_MAX + 1); }
 __host__ __device__ inline int tab_eps(int Qxi) { return tab_cxi(Qxi) + 3 * Qxi; }
-inline int tab_size(int Qp, int Qxi) { return tab_eps(Qxi) + 3 * Qp * Qxi; }
+__host__ __device__ inline int tab_epsf(int Qp, int Qxi) { return tab_eps(Qxi) + 3 * Qp * Qxi; }
+inline int tab_size(int Qp, int Qxi) { return tab_epsf(Qp, Qxi) + Qp * Qxi; }
 // Per-tube FP32 table of the reduced-precision path (floats, starting at TubeDev::tabf): one record of
 // RP_REC floats per velocity s = i Qxi + j, 16-byte aligned, read with vector loads:
 //   R_XI          xi_j

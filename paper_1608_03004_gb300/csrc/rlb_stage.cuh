@@ -228,9 +228,9 @@ struct StageSmem {
   double rate[2][GW];
   double row[2][NG][RW + 1];  // staged velocity rows (double-buffered: written before the first barrier)
   double d1[NG][RW + 1];      // first differences by position, d1[k] = row[k] - row[k-1]
-  double q1[NG][RW + 1];      // their squares
-  double sp[NG][3][GW];       // scaled indicator squares, one triple per pair of adjacent differences
-  double phi[NG][GW];         // WENO correction of each interface, times 6 (weno5_combine6)
+  float2 dd[NG][RW + 1];      // the same differences in double-float (hi, lo)
+  float2 sv[NG][3][GW];       // indicators v = S + e (double-float), one triple per pair of adjacent differences
+  float2 phi[NG][GW];         // WENO correction of each interface, times 6 (double-float)
   int src[RW + 1];            // source cell of each staged position (boundary condition applied)
   double B[NBC][GW];          // equilibrium coefficients B[i (NVc + 1) + k]; last, so that a launch allocates
                               // only the rows its tubes use (stage_smem_bytes)
@@ -335,11 +335,12 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
   const double a = A.a, b = A.b;
   const double* cxi_tab = tab + tab_cxi(Qxi) + A.stage * Qxi;
   double* d1 = sm.d1[g];
-  double* q1 = sm.q1[g];
-  double* sp0 = sm.sp[g][0];
-  double* sp1 = sm.sp[g][1];
-  double* sp2 = sm.sp[g][2];
-  double* phi = sm.phi[g];
+  float2* dd = sm.dd[g];
+  float2* sv0 = sm.sv[g][0];
+  float2* sv1 = sm.sv[g][1];
+  float2* sv2 = sm.sv[g][2];
+  float2* phi = sm.phi[g];
+  const float2* epsf = reinterpret_cast<const float2*>(tab + tab_epsf(Qp, Qxi));
   const int hq = Qxi / 2, upr = hq + (Qxi & 1), U = Qp * upr;
   const int u_end = (part + 1) * U / nparts;
   int buf = 0;
@@ -353,7 +354,8 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
       const int j = h == 0 ? jA : Qxi - 1 - jA;
       const int s = i * Qxi + j;
       double* row = sm.row[buf][g];
-      // stage the row with its first differences and their squares (position k needs k - 1 as well)
+      // stage the row with its first differences, in FP64 and split into double-float (position k needs k - 1
+      // as well)
       {
         const double* src = Fin + (size_t)s * ld;
         for (int k = c; k < RW; k += GW) {
@@ -362,7 +364,8 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
           if (k > 0) {
             const double dk = v - __ldg(src + sm.src[k - 1]);
             d1[k] = dk;
-            q1[k] = dk * dk;
+            const rlbdev::DF q = rlbdev::df_split(dk);
+            dd[k] = make_float2(q.hi, q.lo);
           }
         }
       }
@@ -373,12 +376,12 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
       // c + 2 (toward -x); these are the pairs the TX + 1 interfaces of the tile use
       {
         const int p = c + (fwd ? 1 : 2);
-        const double* et = tab + tab_eps(Qxi) + 3 * s;
-        double sa, sb, sc;
-        rlbdev::weno5_pair_q(q1[p], d1[p] * d1[p + 1], q1[p + 1], fwd, et[0], et[1], et[2], sa, sb, sc);
-        sp0[c] = sa;
-        sp1[c] = sb;
-        sp2[c] = sc;
+        const float2 e = epsf[s], x = dd[p], y = dd[p + 1];
+        rlbdev::DF va, vb, vc;
+        rlbdev::weno5_pair_df({x.x, x.y}, {y.x, y.y}, fwd, {e.x, e.y}, va, vb, vc);
+        sv0[c] = make_float2(va.hi, va.lo);
+        sv1[c] = make_float2(vb.hi, vb.lo);
+        sv2[c] = make_float2(vc.hi, vc.lo);
       }
       group_sync(g);
       // interfaces: interface c lies between cells x0 + c - 1 and x0 + c (row index c + 2 | c + 3); its value
@@ -386,20 +389,27 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
       // (wind toward +x) or d1[c + 4] (toward -x)
       double D = 0.0;
       if (c <= TX) {
-        double G;
+        auto get = [](const float2* a, int k) { const float2 q = a[k]; return rlbdev::DF{q.x, q.y}; };
+        auto neg = [&](int k) { const float2 q = dd[k]; return rlbdev::DF{-q.x, -q.y}; };
+        rlbdev::DF G;
         if (fwd) {
           D = d1[c + 3];
-          G = rlbdev::weno5_combine6(sp0[c], sp1[c + 1], sp2[c + 2], d1[c + 1], d1[c + 2], D, d1[c + 4]);
+          G = rlbdev::weno5_combine6_df(get(sv0, c), get(sv1, c + 1), get(sv2, c + 2), get(dd, c + 1), get(dd, c + 2),
+                                        get(dd, c + 3), get(dd, c + 4));
         } else {
           D = d1[c + 4];
-          G = rlbdev::weno5_combine6(sp0[c + 2], sp1[c + 1], sp2[c], -d1[c + 5], -D, -d1[c + 3], -d1[c + 2]);
+          G = rlbdev::weno5_combine6_df(get(sv0, c + 2), get(sv1, c + 1), get(sv2, c), neg(c + 5), neg(c + 4), neg(c + 3),
+                                        neg(c + 2));
         }
-        phi[c] = G;
+        phi[c] = make_float2(G.hi, G.lo);
       }
       group_sync(g);
       if (cell) {
         const double F = row[c + 3];
-        const double dphi = fma(phi[c + 1] - phi[c], 1.0 / 6.0, D);  // phi holds 6 G
+        // phi holds 6 G: D + (6 G_{x+1/2} - 6 G_{x-1/2}) / 6, the difference taken in double-float
+        const float2 pr = phi[c + 1], pl = phi[c];
+        const rlbdev::DF dG = rlbdev::df_plus({pr.x, pr.y}, {-pl.x, -pl.y});
+        const double dphi = fma(rlbdev::df_widen(dG.hi), 1.0 / 6.0, fma(rlbdev::df_widen(dG.lo), 1.0 / 6.0, D));
         double out = F;
         if (A.stage != 0) out = fma(a, Fn[(size_t)s * ld + x], b * F);  // a = 0 in the first stage
         out = fma(-cxi_tab[j], dphi, out);  // - b dt xi/dx (Phi_{x+1/2} - Phi_{x-1/2})
