@@ -369,6 +369,8 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
           }
         }
       }
+      // the Runge-Kutta input of this row's cell, loaded now so that its latency hides behind the limiter
+      const double fnv = (A.stage != 0 && cell) ? __ldg(Fn + (size_t)s * ld + x) : 0.0;
       group_sync(g);
       const double xi = tab[TAB_XI + j];
       const bool fwd = h == 1;  // the mirror row xi_{Qxi-1-jA} > 0; the first row has xi <= 0
@@ -394,12 +396,12 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
         rlbdev::DF G;
         if (fwd) {
           D = d1[c + 3];
-          G = rlbdev::weno5_combine6_df(get(sv0, c), get(sv1, c + 1), get(sv2, c + 2), get(dd, c + 1), get(dd, c + 2),
-                                        get(dd, c + 3), get(dd, c + 4));
+          G = rlbdev::weno5_combine6_df(get(sv0, c), get(sv1, c + 1), get(sv2, c + 2), get(dd, c + 1),
+                                        get(dd, c + 2), get(dd, c + 3), get(dd, c + 4));
         } else {
           D = d1[c + 4];
-          G = rlbdev::weno5_combine6_df(get(sv0, c + 2), get(sv1, c + 1), get(sv2, c), neg(c + 5), neg(c + 4), neg(c + 3),
-                                        neg(c + 2));
+          G = rlbdev::weno5_combine6_df(get(sv0, c + 2), get(sv1, c + 1), get(sv2, c), neg(c + 5), neg(c + 4),
+                                        neg(c + 3), neg(c + 2));
         }
         phi[c] = make_float2(G.hi, G.lo);
       }
@@ -411,7 +413,7 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
         const rlbdev::DF dG = rlbdev::df_plus({pr.x, pr.y}, {-pl.x, -pl.y});
         const double dphi = fma(rlbdev::df_widen(dG.hi), 1.0 / 6.0, fma(rlbdev::df_widen(dG.lo), 1.0 / 6.0, D));
         double out = F;
-        if (A.stage != 0) out = fma(a, Fn[(size_t)s * ld + x], b * F);  // a = 0 in the first stage
+        if (A.stage != 0) out = fma(a, fnv, b * F);  // a = 0 in the first stage
         out = fma(-cxi_tab[j], dphi, out);  // - b dt xi/dx (Phi_{x+1/2} - Phi_{x-1/2})
         if (T.collide) {
           if (h == 0) {

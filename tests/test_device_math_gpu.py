@@ -98,15 +98,15 @@ def test_weno5_double_float_limiter_matches_oracle(shim):
 
 def test_double_float_split_round_trip(shim):
     """df_split keeps the top 47 significant bits of a double (hi + lo, both truncated): the widened sum is
-    within 2^-46 relative for |d| >= 2^-103, within 2^-23 (hi alone) for 2^-126 <= |d| < 2^-103, and 0 below;
-    zero stays zero and signs are kept."""
+    within 2^-46 relative for |d| >= 2^-80, within 2^-23 for 2^-126 <= |d| < 2^-80 (where lo is subnormal or
+    dropped, and df_widen reads a subnormal float as 0), and 0 below; zero stays zero and signs are kept."""
     rng = np.random.default_rng(3)
     d = rng.normal(size=20000) * 10.0 ** rng.uniform(-40, 30, 20000)
     d = np.concatenate([d, [0.0, -3.0, 1.0, -(2.0 ** -100), 2.0 ** -103, 2.0 ** 127, 1e-39]])
     got = run(shim, 5, d, d.size)
     a = np.abs(d)
-    full, hi_only, tiny = a >= 2.0 ** -103, (a >= 2.0 ** -126) & (a < 2.0 ** -103), a < 2.0 ** -126
-    assert full.sum() > 15000 and hi_only.sum() > 100 and tiny.sum() > 100
+    full, hi_only, tiny = a >= 2.0 ** -80, (a >= 2.0 ** -126) & (a < 2.0 ** -80), a < 2.0 ** -126
+    assert full.sum() > 12000 and hi_only.sum() > 1000 and tiny.sum() > 100
     assert np.all(np.abs(got[full] - d[full]) <= 2.0 ** -46 * a[full])
     assert np.all(np.abs(got[hi_only] - d[hi_only]) <= 2.0 ** -23 * a[hi_only])
     assert np.all(got[tiny] == 0.0)
