@@ -422,17 +422,11 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
 
   // Rows in the order i = 0 .. Qp-1 (outer), then the mirror pairs of directions (xi_jf > 0, xi_jb = -xi_jf),
   // jb = 0 .. Qxi/2 - 1, jf = Qxi - 1 - jb: row jf then row jb; an odd Qxi ends each radial node with its xi = 0
-  // row. The next row's loads are in flight while a row is evaluated.
+  // row. The next row's loads are in flight while a row is evaluated; the walk advances by increments (no
+  // division by Qxi per row).
   const int hq = Qxi / 2;
-  auto row_of = [&](int k) {  // k-th row of the walk
-    const int i = k / Qxi, kk = k - i * Qxi;
-    const int j = kk >= 2 * hq ? hq : ((kk & 1) ? kk >> 1 : Qxi - 1 - (kk >> 1));
-    return i * Qxi + j;
-  };
-  const int Q = Qp * Qxi;
   RpRow ra, rb;
-  rp_load_row<S>(ra, Fin, (size_t)row_of(0) * ld, xl, full, csrc, edge, hsrc);
-  int k = 0;  // row held in ra
+  rp_load_row<S>(ra, Fin, (size_t)(Qxi - 1) * ld, xl, full, csrc, edge, hsrc);  // the walk's first row
   // The record's second float4 (1/ws, ws/6), which the first row of a pair needs at once, is loaded one pair
   // ahead; the rest of the record is needed only after that row's flux differences, which cover its latency.
   float4 nr1 = rec[(size_t)(Qxi - 1) * (RP_REC / 4) + 1];
@@ -441,10 +435,10 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
 #pragma unroll
     for (int q = 0; q < RP_C; ++q) Sm.s0[q] = Sm.s1[q] = Sm.s2[q] = {0.f, 0.f};
     const float* Bi = w.B + (size_t)i * (NVc + 1) * RP_WT + RP_C * lane;
-    for (int jb = 0; jb < hq; ++jb, k += 2) {
+    for (int jb = 0; jb < hq; ++jb) {
       const int jf = Qxi - 1 - jb;
       const int sf = i * Qxi + jf, sbk = i * Qxi + jb;
-      rp_load_row<S>(rb, Fin, (size_t)sbk * ld, xl, full, csrc, edge, hsrc);  // row k + 1
+      rp_load_row<S>(rb, Fin, (size_t)sbk * ld, xl, full, csrc, edge, hsrc);  // the pair's second row
       // the pair's velocity record (of xi_jf > 0): xi, b dt xi/dx per stage, 1/ws, ws/6, moment weights,
       // w^xi P_k(xi)
       const float4* rp = rec + (size_t)sf * (RP_REC / 4);
@@ -479,7 +473,10 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
 #pragma unroll
       for (int q = 0; q < RP_C; ++q) feq[q] = __fadd_rn(E[q], O[q]);
       rp_finish<S>(A, T, ra, dphi, fn, cxi, rt0, rt1, xi, feq, Fout + (size_t)sf * ld, xl, full, stf);
-      if (k + 2 < Q) rp_load_row<S>(ra, Fin, (size_t)row_of(k + 2) * ld, xl, full, csrc, edge, hsrc);
+      {
+        const int snx = jb + 1 < hq ? sf - 1 : ((Qxi & 1) ? i * Qxi + hq : (i + 1) * Qxi + Qxi - 1);
+        if (jb + 1 < hq || (Qxi & 1) || i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)snx * ld, xl, full, csrc, edge, hsrc);
+      }
       // row jb: wind toward -x
       if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sbk * ld, xl, full, Nx);
       rp_flux_diff<false>(rb, lane, iws, ws6, dphi);
@@ -508,8 +505,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       }
       if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sc * ld, xl, full, Nx);
       rp_finish<S>(A, T, ra, zero, fn, 0.f, rt0, rt1, 0.f, feq, Fout + (size_t)sc * ld, xl, full, st);
-      ++k;
-      if (k < Q) rp_load_row<S>(ra, Fin, (size_t)row_of(k) * ld, xl, full, csrc, edge, hsrc);
+      if (i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)((i + 1) * Qxi + Qxi - 1) * ld, xl, full, csrc, edge, hsrc);
       if (T.collide) {
 #pragma unroll
         for (int q = 0; q < RP_C; ++q) rlbdev::df_add(Sm.s0[q], {st[q], 0.f});
