@@ -313,9 +313,10 @@ rlb_status ensure_series_tables(int dev) {
   for (const void* k : rp) {
     RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)rp_smem_bytes(QP_MAX * (NV_MAX + 1))));
-    // the whole carveout as shared memory, so that shared memory never limits the CTAs per SM below the
-    // register limit
-    RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    // carveout: enough shared memory for the four CTAs per SM that the registers allow with the default orders
+    // (Np = 2, Nv = 5), the rest left to L1, which holds the per-velocity records and the register spills
+    const int pct = (int)((100 * 4 * (rp_smem_bytes(rp_brows(3, 2, 5)) + 1024) + 228 * 1024 - 1) / (228 * 1024));
+    RLB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
   }
   RLB_CUDA(cudaFuncSetAttribute((const void*)rlb_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(AdjSmem)));

@@ -127,16 +127,20 @@ struct StageArgsRP {
   int brows;           // coefficient rows per warp region: max over the tubes of Qp (Nv + 1)
 };
 
-// Shared memory of one warp tile (lane-private columns 4 lane .. 4 lane + 3): the cells' FP32 equilibrium
-// coefficients B[i (Nv + 1) + k][cell] (brows rows), then their five moment sums as (hi, lo) float pairs
-// M[f][cell].
+// Shared memory of one warp tile (lane-private columns 4 lane .. 4 lane + 3), rp_rows(brows) rows of RP_WT
+// floats: the cells' FP32 equilibrium coefficients B[i][k] of radial node i at row rp_brow(i, k) (node 0's rows
+// last), and their five moment sums as (hi, lo) float pairs M[f][cell] from node 0's first row on: node 0's
+// coefficients are no longer read once M is first written (after node 0's walk), so M takes their place and
+// RP_MEXTRA rows beyond them.
+constexpr int RP_MEXTRA = 10 - 6;  // M's 10 float rows over the Nv + 1 >= 6 rows of node 0
+__host__ __device__ constexpr int rp_rows(int brows) { return brows + RP_MEXTRA; }
+__device__ __forceinline__ int rp_brow(int i, int k, int Qp, int nk) { return (i == 0 ? Qp - 1 : i - 1) * nk + k; }
 struct RpWarp {
   float* B;
-  float2* M;
 };
 // Dynamic shared memory of a CTA for `brows` coefficient rows.
 __host__ __device__ constexpr size_t rp_smem_bytes(int brows) {
-  return (size_t)RP_WARPS * RP_WT * (brows + 10) * sizeof(float);
+  return (size_t)RP_WARPS * RP_WT * rp_rows(brows) * sizeof(float);
 }
 // Coefficient rows of a tube as the kernel stores them.
 __host__ __device__ inline int rp_brows(int Qp, int Np, int Nv) { return Qp * ((Np == 2 && Nv == 5) ? 6 : NV_MAX + 1); }
@@ -167,9 +171,9 @@ __device__ void cell_coeffs_rp(const TubeDev* Tg, const double* tab, int Qp, con
           B0 = fma(G, 1.0, B0);
           sq *= Tt;
         }
-        w.B[(i * (NVc + 1)) * RP_WT + col] = (float)B0;
+        w.B[rp_brow(i, 0, Qp, NVc + 1) * RP_WT + col] = (float)B0;
 #pragma unroll
-        for (int k = 1; k <= NVc; ++k) w.B[(i * (NVc + 1) + k) * RP_WT + col] = 0.f;
+        for (int k = 1; k <= NVc; ++k) w.B[rp_brow(i, k, Qp, NVc + 1) * RP_WT + col] = 0.f;
       }
     }
     rt0 = (float)bdt_itau;
@@ -204,7 +208,7 @@ __device__ void cell_coeffs_rp(const TubeDev* Tg, const double* tab, int Qp, con
     }
     if (i < Qp) {
 #pragma unroll
-      for (int k = 0; k <= NVc; ++k) w.B[(i * (NVc + 1) + k) * RP_WT + col] = (float)B[k];
+      for (int k = 0; k <= NVc; ++k) w.B[rp_brow(i, k, Qp, NVc + 1) * RP_WT + col] = (float)B[k];
     }
   }
   const double r0 = ok ? bdt_itau * gam : 0.0;
@@ -358,14 +362,15 @@ __device__ __forceinline__ void rp_sums_pair(RpSums& S, const float (&sf)[RP_C],
   }
 }
 
-// Fold the radial sums of node i into the five moments (double-float pairs in the lane's shared columns):
-// N0 += pbar S0, Nx += pbar S1, T00 += pbar^2 S0, T0x += pbar^2 S1, Txx += pbar^2 S2.
-__device__ __forceinline__ void rp_fold(const RpWarp& w, int lane, const RpSums& S, float p1h, float p1l, float p2h,
-                                        float p2l) {
+// Fold the radial sums of node i into the five moments (double-float pairs M in the lane's shared columns):
+// N0 += pbar S0, Nx += pbar S1, T00 += pbar^2 S0, T0x += pbar^2 S1, Txx += pbar^2 S2; the first fold starts from
+// zero (M then still holds node 0's coefficients).
+__device__ __forceinline__ void rp_fold(float2* M, int lane, bool first, const RpSums& S, float p1h, float p1l,
+                                        float p2h, float p2l) {
 #pragma unroll
   for (int f = 0; f < 5; ++f) {
-    float4* mp = reinterpret_cast<float4*>(w.M + f * RP_WT + RP_C * lane);
-    const float4 u0 = mp[0], u1 = mp[1];
+    float4* mp = reinterpret_cast<float4*>(M + f * RP_WT + RP_C * lane);
+    const float4 u0 = first ? make_float4(0.f, 0.f, 0.f, 0.f) : mp[0], u1 = first ? make_float4(0.f, 0.f, 0.f, 0.f) : mp[1];
     rlbdev::DF m[RP_C] = {{u0.x, u0.y}, {u0.z, u0.w}, {u1.x, u1.y}, {u1.z, u1.w}};
     const float wh = f < 2 ? p1h : p2h, wl = f < 2 ? p1l : p2l;
 #pragma unroll
@@ -414,11 +419,8 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       cell_coeffs_rp<NPc, NVc>(A.tubes + T.index, tab, Qp, mom, bdt_itau, xl + q < Nx ? A.flag : nullptr,
                                w, RP_C * lane + q, rt0[q], rt1[q]);
     }
-#pragma unroll
-    for (int q = 0; q < RP_C; ++q)
-#pragma unroll
-      for (int f = 0; f < 5; ++f) w.M[f * RP_WT + RP_C * lane + q] = make_float2(0.f, 0.f);
   }
+  float2* const M = reinterpret_cast<float2*>(w.B + (size_t)rp_brow(0, 0, Qp, NVc + 1) * RP_WT);
 
   // Rows in the order i = 0 .. Qp-1 (outer), then the mirror pairs of directions (xi_jf > 0, xi_jb = -xi_jf),
   // jb = 0 .. Qxi/2 - 1, jf = Qxi - 1 - jb: row jf then row jb; an odd Qxi ends each radial node with its xi = 0
@@ -434,7 +436,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
     RpSums Sm;
 #pragma unroll
     for (int q = 0; q < RP_C; ++q) Sm.s0[q] = Sm.s1[q] = Sm.s2[q] = {0.f, 0.f};
-    const float* Bi = w.B + (size_t)i * (NVc + 1) * RP_WT + RP_C * lane;
+    const float* Bi = w.B + (size_t)rp_brow(i, 0, Qp, NVc + 1) * RP_WT + RP_C * lane;
     for (int jb = 0; jb < hq; ++jb) {
       const int jf = Qxi - 1 - jb;
       const int sf = i * Qxi + jf, sbk = i * Qxi + jb;
@@ -513,7 +515,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
     }
     if (T.collide) {
       const float4 p = rec[(size_t)(i * Qxi) * (RP_REC / 4) + 1];  // R_P1 .. R_P2 + 1 of radial node i
-      rp_fold(w, lane, Sm, p.z, p.w, rec[(size_t)(i * Qxi) * (RP_REC / 4) + 2].x,
+      rp_fold(M, lane, i == 0, Sm, p.z, p.w, rec[(size_t)(i * Qxi) * (RP_REC / 4) + 2].x,
               rec[(size_t)(i * Qxi) * (RP_REC / 4) + 2].y);
     }
   }
@@ -524,7 +526,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       if (xl + q < Nx) {
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
-          const float2 m = w.M[f * RP_WT + RP_C * lane + q];
+          const float2 m = M[f * RP_WT + RP_C * lane + q];
           A.Mout[f * A.nxtot + T.xoff + xl + q] = (double)m.x + (double)m.y;
         }
       }
@@ -535,8 +537,7 @@ template <typename S, int SCHED>
 __global__ void __launch_bounds__(RP_NT, 4) rlb_stage_rp_kernel(StageArgsRP A) {
   extern __shared__ __align__(16) float stage_rp_smem[];
   const int warp = threadIdx.x / 32;
-  float* base = stage_rp_smem + (size_t)warp * RP_WT * (A.brows + 10);
-  const RpWarp w{base, reinterpret_cast<float2*>(base + (size_t)RP_WT * A.brows)};
+  const RpWarp w{stage_rp_smem + (size_t)warp * RP_WT * rp_rows(A.brows)};
   for_each_tile(A.ngroups, SCHED, A.counter, [&](int grp) {
     const int wt = grp * RP_WARPS + warp;
     if (wt < A.nwt) {  // uniform over the warp
