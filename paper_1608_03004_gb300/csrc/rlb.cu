@@ -341,7 +341,7 @@ struct rlb_ctx {
   long long nxtot = 0;
   TubeDev* d_tubes = nullptr;
   int2* d_tiles = nullptr;
-  int2* d_wtiles = nullptr;    // reduced storage: warp tiles of RP_WT cells
+  int2* d_wtiles = nullptr;    // reduced storage: warp tiles of RP_OUT cells
   int nwt = 0;
   int brows = 0;               // reduced storage: coefficient rows per warp region of the stage kernel
   size_t stage_smem = 0;       // FP64: dynamic shared memory of the stage kernel (coefficient rows in use)
@@ -473,7 +473,7 @@ bool fill_tube_tables(const rlb_tube& t, double* pb, double* wp, double* xi, dou
   return true;
 }
 
-// Tiles of `width` cells of every tube (TX for the FP64 kernels, RP_WT warp tiles for the reduced-precision
+// Tiles of `width` cells of every tube (TX for the FP64 kernels, RP_OUT warp tiles for the reduced-precision
 // kernel): most expensive tubes first (RLB_ORDER_COST), or the tubes interleaved tile by tile
 // (RLB_ORDER_INTERLEAVE).
 std::vector<int2> build_tiles(const std::vector<rlb_tube>& tubes, int order, int width = TX) {
@@ -622,7 +622,7 @@ rlb_status create(rlb_handle* out, const rlb_tube* tubes, int32_t ntubes, const 
   RLB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   RLB_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
   if (h->storage != RLB_STORAGE_F64) {
-    const std::vector<int2> wt = build_tiles(h->tubes, RLB_ORDER_COST, RP_WT);
+    const std::vector<int2> wt = build_tiles(h->tubes, RLB_ORDER_COST, RP_OUT);
     h->nwt = (int)wt.size();
     for (const rlb_tube& t : h->tubes) h->brows = std::max(h->brows, rp_brows(t.Qp, t.Np, t.Nv));
     RLB_CUDA(cudaMalloc(&h->d_wtiles, sizeof(int2) * wt.size()));
@@ -979,7 +979,7 @@ rlb_status rlb_set_launch(rlb_handle h, const rlb_launch* cfg) {
                              h->stream));
     std::vector<int2> wt;
     if (h->d_wtiles) {
-      wt = build_tiles(h->tubes, cfg->order, RP_WT);
+      wt = build_tiles(h->tubes, cfg->order, RP_OUT);
       RLB_CUDA(cudaMemcpyAsync(h->d_wtiles, wt.data(), sizeof(int2) * wt.size(), cudaMemcpyHostToDevice, h->stream));
     }
     RLB_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope

@@ -5,21 +5,22 @@
 // anonymous namespace.
 //
 // Built for instruction throughput and bandwidth rather than for the FP64 pipe:
-//  - a warp owns a tile of RP_WT = 128 cells and walks all velocity rows of it; each lane holds RP_C = 4
-//    consecutive cells of a row in registers (one 16-byte load and store per lane and row in FP32, 8 bytes in
-//    BF16), takes the three neighbour values on each side from the adjacent lanes by shuffles (the edge lanes
-//    load the tile's halo, boundary condition applied) and evaluates its pairs of WENO5 indicators, its five
-//    interface values, the collision and the Runge-Kutta combination without shared memory or barriers;
-//  - the per-velocity constants are one 24-float record (six vector loads, uniform over the warp);
+//  - a warp holds RP_WT = 128 consecutive cells of a row, RP_C = 4 per lane in registers (one 16-byte load and
+//    store per lane and row in FP32, 8 bytes in BF16), and advances the RP_OUT = 120 cells of lanes 1 .. 30:
+//    lanes 0 and 31 hold the 4-cell halo on each side. Each lane forms the differences, WENO5 indicator pairs and
+//    interface values it owns, once in the warp, takes the few it needs from its neighbours by shuffles, and
+//    evaluates the collision and the Runge-Kutta combination without shared memory or barriers;
+//  - the per-velocity constants are one 24-float record (vector loads, uniform over the warp);
 //  - the moments of a stage's input are not re-read: the stage that wrote F_in accumulated them while
 //    storing it and left 5 FP64 moments per cell (M_in); this stage does the same for F_out (M_out);
 //  - the next row's loads are in flight while a row is evaluated, and F^n is loaded at the start of a row's
 //    evaluation (it is needed only at its end);
 //  - FP64 work is per cell only (Landau frame, Legendre series, equilibrium coefficients), kept by each lane
 //    for its own cells in shared memory, where the lane also keeps its cells' five moment sums between
-//    directions (lane-private columns: no barrier).
-// Rows are walked radial-innermost (j outer, i = 0 .. Qp-1 inner; s = i Qxi + j) so that the radial partial
-// sums sum_i F pbar_i and sum_i F pbar_i^2 of one direction xi_j are folded into the five moments once per j.
+//    radial nodes (lane-private columns: no barrier).
+// Rows are walked radial node by radial node, each node's directions in mirror pairs (xi, -xi), so that a pair
+// shares its velocity record and the even and odd parts of its equilibrium, and the radial sums of a node are
+// folded into the five moments once per node.
 #pragma once
 
 // Loads of the streamed state rows bypass L1 (ld.global.nc.L1::no_allocate): every row is read once per stage,
@@ -100,14 +101,15 @@ __device__ __forceinline__ void st_s<__nv_bfloat16>(__nv_bfloat16* p, float v) {
   *p = __float2bfloat16_rn(v);
 }
 
-constexpr int RP_C = 4;               // cells per lane
-constexpr int RP_WT = 32 * RP_C;      // cells per warp tile
-constexpr int RP_WARPS = 4;           // warps per CTA, each on its own warp tile
-constexpr int RP_NT = 32 * RP_WARPS;  // threads per CTA
+constexpr int RP_C = 4;                   // cells per lane
+constexpr int RP_WT = 32 * RP_C;          // cells a warp holds
+constexpr int RP_OUT = RP_WT - 2 * RP_C;  // cells a warp tile advances: lanes 1 .. 30 (lanes 0 and 31 hold the halo)
+constexpr int RP_WARPS = 4;               // warps per CTA, each on its own warp tile
+constexpr int RP_NT = 32 * RP_WARPS;      // threads per CTA
 
 struct StageArgsRP {
   const TubeDev* tubes;
-  const int2* wtiles;  // warp tiles (tube, first cell), RP_WT cells each
+  const int2* wtiles;  // warp tiles (tube, first cell), RP_OUT cells each
   int nwt;             // warp tiles
   const void* Fn;      // state at the start of the step (read at the cell only)
   const void* Fin;     // stage input (read with halo)
@@ -216,16 +218,16 @@ __device__ void cell_coeffs_rp(const TubeDev* Tg, const double* tab, int Qp, con
   rt1 = (float)(r0 * beta);
 }
 
-// One velocity row as a lane holds it: its RP_C cells and the tile's halo (edge lanes only: lane 0 holds cells
-// x0-3 .. x0-1, lane 31 cells x0+RP_WT .. x0+RP_WT+2, boundary condition applied).
+// One velocity row as a lane holds it: its RP_C cells xl .. xl+3 (xl = x0 - RP_C + RP_C lane, so that lane 0
+// holds the tile's left halo x0-4 .. x0-1 and lane 31 its right halo x0+RP_OUT .. +3).
 struct RpRow {
   float v[RP_C];
-  float h[3];
 };
 
+// A row's cells: one vector load where the warp's 128 cells all lie inside the tube (full), otherwise one load
+// per cell from its source under the boundary condition (positions left of -3 are never used and read -3).
 template <typename S>
-__device__ __forceinline__ void rp_load_row(RpRow& r, const S* Fin, size_t row, int xl, bool full,
-                                            const int (&csrc)[RP_C], bool edge, const int (&hsrc)[3]) {
+__device__ __forceinline__ void rp_load_row(RpRow& r, const S* Fin, size_t row, int xl, bool full, const TubeDev& T) {
   const S* src = Fin + row;
   if (full) {
     const float4 t = ld4(src + xl);
@@ -235,16 +237,16 @@ __device__ __forceinline__ void rp_load_row(RpRow& r, const S* Fin, size_t row, 
     r.v[3] = t.w;
   } else {
 #pragma unroll
-    for (int q = 0; q < RP_C; ++q) r.v[q] = ld_s<S>(src + csrc[q]);
+    for (int q = 0; q < RP_C; ++q) r.v[q] = ld_s<S>(src + map_cell(max(xl + q, -HALO), T.Nx, T.bc, T.ld));
   }
-#pragma unroll
-  for (int h = 0; h < 3; ++h) r.h[h] = edge ? ld_s<S>(src + hsrc[h]) : 0.f;
 }
 
-// F^n of a lane's cells (stages 2 and 3 only).
+// F^n of a lane's cells (stages 2 and 3 only; output lanes only, whose cells are >= 0).
 template <typename S>
-__device__ __forceinline__ void rp_load_fn(float (&fn)[RP_C], const S* Fn, size_t row, int xl, bool full, int Nx) {
+__device__ __forceinline__ void rp_load_fn(float (&fn)[RP_C], const S* Fn, size_t row, int xl, bool full, int Nx,
+                                           bool out) {
   const S* fs = Fn + row;
+  if (!out) return;
   if (full) {
     const float4 t = ld4(fs + xl);
     fn[0] = t.x;
@@ -257,73 +259,90 @@ __device__ __forceinline__ void rp_load_fn(float (&fn)[RP_C], const S* Fn, size_
   }
 }
 
-// Flux differences Phi(q + 1/2) - Phi(q - 1/2) of a lane's cells q = 0 .. RP_C-1 for a wind toward +x (FWD) or
-// toward -x, from the row and its neighbours (shuffles; the edge lanes take the halo). The window w holds the
-// nine positions the five interfaces X = 0 .. 4 of the lane reach (interface X lies between cells X-1 and X):
-// -3 .. 5 toward +x, -2 .. 6 toward -x; d[k] = w[k+1] - w[k] is the difference at position k - 2 (toward +x) or
-// k - 1 (toward -x), and d[q + 2] is in both cases the jump between the upwind cells of interfaces q + 1 and q.
-// Each interface value is the upwind cell plus G, G from the three candidate stencils' indicators on the
-// differences scaled by 1/ws (the limiter acts on F / ws): the combination of the scaled differences returns
-// 6 G / ws, and the flux difference scales it back with ws6 = ws / 6 in its one FMA.
-template <bool FWD>
-__device__ __forceinline__ void rp_flux_diff(const RpRow& r, int lane, float iws, float ws6, float (&dphi)[RP_C]) {
-  constexpr unsigned ALL = 0xffffffffu;
-  float w[9];
-  if (FWD) {
-    const float l1 = __shfl_up_sync(ALL, r.v[1], 1), l2 = __shfl_up_sync(ALL, r.v[2], 1),
-                l3 = __shfl_up_sync(ALL, r.v[3], 1);
-    const float q0 = __shfl_down_sync(ALL, r.v[0], 1), q1 = __shfl_down_sync(ALL, r.v[1], 1);
-    w[0] = lane == 0 ? r.h[0] : l1;
-    w[1] = lane == 0 ? r.h[1] : l2;
-    w[2] = lane == 0 ? r.h[2] : l3;
-#pragma unroll
-    for (int q = 0; q < RP_C; ++q) w[3 + q] = r.v[q];
-    w[7] = lane == 31 ? r.h[0] : q0;
-    w[8] = lane == 31 ? r.h[1] : q1;
-  } else {
-    const float l2 = __shfl_up_sync(ALL, r.v[2], 1), l3 = __shfl_up_sync(ALL, r.v[3], 1);
-    const float q0 = __shfl_down_sync(ALL, r.v[0], 1), q1 = __shfl_down_sync(ALL, r.v[1], 1),
-                q2 = __shfl_down_sync(ALL, r.v[2], 1);
-    w[0] = lane == 0 ? r.h[1] : l2;
-    w[1] = lane == 0 ? r.h[2] : l3;
-#pragma unroll
-    for (int q = 0; q < RP_C; ++q) w[2 + q] = r.v[q];
-    w[6] = lane == 31 ? r.h[0] : q0;
-    w[7] = lane == 31 ? r.h[1] : q1;
-    w[8] = lane == 31 ? r.h[2] : q2;
-  }
-  float d[8], dd[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    d[k] = __fsub_rn(w[k + 1], w[k]);
-    dd[k] = __fmul_rn(d[k], iws);
-  }
-  // indicator squares of the seven pairs of adjacent differences the interfaces use, each pair taken in wind
-  // order: (dd[t], dd[t+1]) toward +x, (dd[t+1], dd[t]) toward -x (an indicator is even in the differences)
-  float sa[7], sb[7], sc[7];
-#pragma unroll
-  for (int t = 0; t < 7; ++t)
-    rlbdev::weno5_pair(FWD ? dd[t] : dd[t + 1], FWD ? dd[t + 1] : dd[t], true, rlbdev::EPS_A, rlbdev::EPS_B,
-                       rlbdev::EPS_C, sa[t], sb[t], sc[t]);
-  float G6[5];  // 6 G / ws of each interface
-#pragma unroll
-  for (int X = 0; X < 5; ++X) {
-    if (FWD)
-      G6[X] = rlbdev::weno5_combine6(sa[X], sb[X + 1], sc[X + 2], dd[X], dd[X + 1], dd[X + 2], dd[X + 3]);
-    else
-      G6[X] = rlbdev::weno5_combine6(sa[X + 2], sb[X + 1], sc[X], -dd[X + 3], -dd[X + 2], -dd[X + 1], -dd[X]);
-  }
-#pragma unroll
-  for (int q = 0; q < RP_C; ++q) dphi[q] = fmaf(__fsub_rn(G6[q + 1], G6[q]), ws6, d[q + 2]);
+// The first and the last of rlbdev::weno5_pair's squares alone (fwd = true), with the same operations, so the
+// same values: sA = (C0 (SL(x, y) + 3eps))^2 and sC = (C2 (SR(x, y) + 3eps))^2.
+__device__ __forceinline__ float weno5_square_a(float x, float y) {
+  using namespace rlbdev;
+  const float qx = mul_x(x, x), pxy = mul_x(x, y), qy = mul_x(y, y);
+  const float u = fmaf(float(4.0 * C0), qx, fmaf(float(-11.0 * C0), pxy, fmaf(float(10.0 * C0), qy, EPS_A)));
+  return mul_x(u, u);
+}
+__device__ __forceinline__ float weno5_square_c(float x, float y) {
+  using namespace rlbdev;
+  const float qx = mul_x(x, x), pxy = mul_x(x, y), qy = mul_x(y, y);
+  const float u = fmaf(float(10.0 * C2), qx, fmaf(float(-11.0 * C2), pxy, fmaf(float(4.0 * C2), qy, EPS_C)));
+  return mul_x(u, u);
 }
 
-// F_out = a F^n + b F - cxi dphi + rate (feq - F) of a lane's cells, rounded to storage and stored; returns the
-// stored values in st.
+// Flux differences Phi(q + 1/2) - Phi(q - 1/2) of a lane's cells q = 0 .. RP_C-1 for a wind toward +x (FWD) or
+// toward -x. Interface X lies between cells X-1 and X; its value is the upwind cell (X-1 toward +x, X toward -x)
+// plus G, G from the three candidate stencils' indicators on the differences D(k) = F(k) - F(k-1) scaled by 1/ws
+// (the limiter acts on F / ws): the combination of the scaled differences returns 6 G / ws, and the flux
+// difference scales it back with ws6 = ws / 6 in its one FMA.
+// Every pair of adjacent differences and every interface is evaluated once in the warp: a lane with cells
+// xl .. xl+3 owns the differences D(xl .. xl+3), the pairs (D(k), D(k+1)) at k = xl .. xl+3 (toward +x) or
+// xl+1 .. xl+4 (toward -x), and the interfaces xl+1 .. xl+4 (the right faces of its cells); what its
+// interfaces need from beyond (one indicator square and up to three differences of a neighbour lane, and the
+// interface xl from the left lane) comes by shuffles. Toward +x interface X takes the pairs at X-2 (sa), X-1
+// (sb) and X (sc) and the differences D(X-2 .. X+1); toward -x the pairs at X+1 (sa), X (sb), X-1 (sc) and
+// the differences -D(X+2 .. X-1) in wind order. The edge lanes' own outputs are wrong (no neighbour beyond) and
+// unused: what lanes 1 and 30 take from them involves their own cells only.
+template <bool FWD>
+__device__ __forceinline__ void rp_flux_diff(const RpRow& r, float iws, float ws6, float (&dphi)[RP_C]) {
+  constexpr unsigned ALL = 0xffffffffu;
+  float D[RP_C], dd[RP_C];
+  D[0] = __fsub_rn(r.v[0], __shfl_up_sync(ALL, r.v[3], 1));
+#pragma unroll
+  for (int q = 1; q < RP_C; ++q) D[q] = __fsub_rn(r.v[q], r.v[q - 1]);
+#pragma unroll
+  for (int q = 0; q < RP_C; ++q) dd[q] = __fmul_rn(D[q], iws);
+  // D(xl+4), D(xl+5) (and toward -x D(xl+6)) from the right lane, scaled here as that lane scales them
+  const float D4 = __shfl_down_sync(ALL, D[0], 1), D5 = __shfl_down_sync(ALL, D[1], 1);
+  const float dd4 = __fmul_rn(D4, iws), dd5 = __fmul_rn(D5, iws);
+  float sa[RP_C], sb[RP_C], sc[RP_C], G6[RP_C + 1];
+  if (FWD) {
+    const float ddn[RP_C + 1] = {dd[0], dd[1], dd[2], dd[3], dd4};
+#pragma unroll
+    for (int q = 0; q < RP_C; ++q)
+      rlbdev::weno5_pair(ddn[q], ddn[q + 1], true, rlbdev::EPS_A, rlbdev::EPS_B, rlbdev::EPS_C, sa[q], sb[q], sc[q]);
+    // the neighbours' indicator squares this lane needs, formed here from their differences as those lanes form
+    // them (same operations, same values): sa of the pair at xl-1, sc of the pair at xl+4
+    const float ddm1 = __shfl_up_sync(ALL, dd[3], 1);
+    const float sam1 = weno5_square_a(ddm1, dd[0]), sc4 = weno5_square_c(dd4, dd5);
+    G6[1] = rlbdev::weno5_combine6(sam1, sb[0], sc[1], ddm1, dd[0], dd[1], dd[2]);
+    G6[2] = rlbdev::weno5_combine6(sa[0], sb[1], sc[2], dd[0], dd[1], dd[2], dd[3]);
+    G6[3] = rlbdev::weno5_combine6(sa[1], sb[2], sc[3], dd[1], dd[2], dd[3], dd4);
+    G6[4] = rlbdev::weno5_combine6(sa[2], sb[3], sc4, dd[2], dd[3], dd4, dd5);
+  } else {
+    const float D6 = __shfl_down_sync(ALL, D[2], 1);
+    const float dd6 = __fmul_rn(D6, iws);
+    const float ddn[RP_C + 2] = {dd[1], dd[2], dd[3], dd4, dd5, dd6};
+    // pair q at k = xl+1+q, taken in wind order (D(k+1), D(k)): an indicator is even in the differences
+#pragma unroll
+    for (int q = 0; q < RP_C; ++q)
+      rlbdev::weno5_pair(ddn[q + 1], ddn[q], true, rlbdev::EPS_A, rlbdev::EPS_B, rlbdev::EPS_C, sa[q], sb[q], sc[q]);
+    // sc of the pair at xl and sa of the pair at xl+5, formed here as the neighbour lanes form them
+    const float scm1 = weno5_square_c(dd[1], dd[0]), sa4 = weno5_square_a(dd6, dd5);
+    G6[1] = rlbdev::weno5_combine6(sa[1], sb[0], scm1, -dd[3], -dd[2], -dd[1], -dd[0]);
+    G6[2] = rlbdev::weno5_combine6(sa[2], sb[1], sc[0], -dd4, -dd[3], -dd[2], -dd[1]);
+    G6[3] = rlbdev::weno5_combine6(sa[3], sb[2], sc[1], -dd5, -dd4, -dd[3], -dd[2]);
+    G6[4] = rlbdev::weno5_combine6(sa4, sb[3], sc[2], -dd6, -dd5, -dd4, -dd[3]);
+  }
+  G6[0] = __shfl_up_sync(ALL, G6[4], 1);  // interface xl, the left lane's last
+  // the upwind cells of interfaces q+1 and q differ by D(xl+q) toward +x and by D(xl+q+1) toward -x
+#pragma unroll
+  for (int q = 0; q < RP_C; ++q)
+    dphi[q] = fmaf(__fsub_rn(G6[q + 1], G6[q]), ws6, FWD ? D[q] : (q + 1 < RP_C ? D[q + 1] : D4));
+}
+
+// F_out = a F^n + b F - cxi dphi + rate (feq - F) of a lane's cells, rounded to storage and stored by the output
+// lanes (out); returns the values in st.
 template <typename S>
 __device__ __forceinline__ void rp_finish(const StageArgsRP& A, const TubeDev& T, const RpRow& r,
                                           const float (&dphi)[RP_C], const float (&fn)[RP_C], float cxi,
                                           const float (&rt0)[RP_C], const float (&rt1)[RP_C], float xi,
-                                          const float (&feq)[RP_C], S* dst, int xl, bool full, float (&st)[RP_C]) {
+                                          const float (&feq)[RP_C], S* dst, int xl, bool full, bool out,
+                                          float (&st)[RP_C]) {
 #pragma unroll
   for (int q = 0; q < RP_C; ++q) {
     const float F = r.v[q];
@@ -332,6 +351,7 @@ __device__ __forceinline__ void rp_finish(const StageArgsRP& A, const TubeDev& T
     if (T.collide) o = fmaf(fmaf(-rt1[q], xi, rt0[q]), __fsub_rn(feq[q], F), o);
     st[q] = rnd_s<S>(o);
   }
+  if (!out) return;
   if (full) {
     st4(dst + xl, make_float4(st[0], st[1], st[2], st[3]));
   } else {
@@ -392,16 +412,10 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
   const S* Fin = static_cast<const S*>(A.Fin) + T.off;
   const S* Fn = static_cast<const S*>(A.Fn) + T.off;
   S* Fout = static_cast<S*>(A.Fout) + T.off;
-  const int xl = x0 + RP_C * lane;            // first cell of this lane
-  const bool full = x0 + RP_WT <= Nx;         // uniform over the warp
-  // sources of the halo (lane 0: x0-3 .. x0-1, lane 31: x0+RP_WT .. +2) and, for a partial tile, of the lane's
-  // positions: boundary condition applied, always inside [0, Nx)
-  const bool edge = lane == 0 || lane == 31;
-  int hsrc[3], csrc[RP_C];
-#pragma unroll
-  for (int h = 0; h < 3; ++h) hsrc[h] = map_cell(lane == 0 ? x0 - 3 + h : x0 + RP_WT + h, Nx, T.bc, ld);
-#pragma unroll
-  for (int q = 0; q < RP_C; ++q) csrc[q] = map_cell(xl + q, Nx, T.bc, ld);
+  // the tile's output cells x0 .. x0 + RP_OUT - 1 belong to lanes 1 .. 30; lanes 0 and 31 hold the halo
+  const int xl = x0 - RP_C + RP_C * lane;               // first cell of this lane
+  const bool out = lane >= 1 && lane <= 30;
+  const bool full = x0 >= RP_C && x0 - RP_C + RP_WT <= Nx;  // all the warp's cells inside the tube (uniform)
 
   // per-cell FP64 phase
   float rt0[RP_C], rt1[RP_C];
@@ -411,13 +425,14 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
     const double bdt_itau = A.bd * T.dt * T.inv_tau;
 #pragma unroll 1
     for (int q = 0; q < RP_C; ++q) {
-      double mom[5] = {1.0, 0.0, 3.0, 0.0, 1.0};  // a rest state for positions past the tube's end
-      if (xl + q < Nx) {
+      double mom[5] = {1.0, 0.0, 3.0, 0.0, 1.0};  // a rest state for the halo lanes and past the tube's end
+      const bool own = out && xl + q < Nx;
+      if (own) {
 #pragma unroll
         for (int f = 0; f < 5; ++f) mom[f] = A.Min[f * A.nxtot + T.xoff + xl + q];
       }
-      cell_coeffs_rp<NPc, NVc>(A.tubes + T.index, tab, Qp, mom, bdt_itau, xl + q < Nx ? A.flag : nullptr,
-                               w, RP_C * lane + q, rt0[q], rt1[q]);
+      cell_coeffs_rp<NPc, NVc>(A.tubes + T.index, tab, Qp, mom, bdt_itau, own ? A.flag : nullptr, w,
+                               RP_C * lane + q, rt0[q], rt1[q]);
     }
   }
   float2* const M = reinterpret_cast<float2*>(w.B + (size_t)rp_brow(0, 0, Qp, NVc + 1) * RP_WT);
@@ -428,7 +443,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
   // division by Qxi per row).
   const int hq = Qxi / 2;
   RpRow ra, rb;
-  rp_load_row<S>(ra, Fin, (size_t)(Qxi - 1) * ld, xl, full, csrc, edge, hsrc);  // the walk's first row
+  rp_load_row<S>(ra, Fin, (size_t)(Qxi - 1) * ld, xl, full, T);  // the walk's first row
   // The record's second float4 (1/ws, ws/6), which the first row of a pair needs at once, is loaded one pair
   // ahead; the rest of the record is needed only after that row's flux differences, which cover its latency.
   float4 nr1 = rec[(size_t)(Qxi - 1) * (RP_REC / 4) + 1];
@@ -440,7 +455,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
     for (int jb = 0; jb < hq; ++jb) {
       const int jf = Qxi - 1 - jb;
       const int sf = i * Qxi + jf, sbk = i * Qxi + jb;
-      rp_load_row<S>(rb, Fin, (size_t)sbk * ld, xl, full, csrc, edge, hsrc);  // the pair's second row
+      rp_load_row<S>(rb, Fin, (size_t)sbk * ld, xl, full, T);  // the pair's second row
       // the pair's velocity record (of xi_jf > 0): xi, b dt xi/dx per stage, 1/ws, ws/6, moment weights,
       // w^xi P_k(xi)
       const float4* rp = rec + (size_t)sf * (RP_REC / 4);
@@ -456,8 +471,8 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       const float iws = rv[R_IWS], ws6 = rv[R_WS6];
       float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C], dphi[RP_C], stf[RP_C], stb[RP_C];
       // row jf: wind toward +x
-      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx);
-      rp_flux_diff<true>(ra, lane, iws, ws6, dphi);
+      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx, out);
+      rp_flux_diff<true>(ra, iws, ws6, dphi);
       // even and odd Legendre parts of the pair's equilibria: feq(+xi) = E + O, feq(-xi) = E - O
       float E[RP_C] = {0.f, 0.f, 0.f, 0.f}, O[RP_C] = {0.f, 0.f, 0.f, 0.f};
       if (T.collide) {
@@ -474,17 +489,17 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       }
 #pragma unroll
       for (int q = 0; q < RP_C; ++q) feq[q] = __fadd_rn(E[q], O[q]);
-      rp_finish<S>(A, T, ra, dphi, fn, cxi, rt0, rt1, xi, feq, Fout + (size_t)sf * ld, xl, full, stf);
+      rp_finish<S>(A, T, ra, dphi, fn, cxi, rt0, rt1, xi, feq, Fout + (size_t)sf * ld, xl, full, out, stf);
       {
         const int snx = jb + 1 < hq ? sf - 1 : ((Qxi & 1) ? i * Qxi + hq : (i + 1) * Qxi + Qxi - 1);
-        if (jb + 1 < hq || (Qxi & 1) || i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)snx * ld, xl, full, csrc, edge, hsrc);
+        if (jb + 1 < hq || (Qxi & 1) || i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)snx * ld, xl, full, T);
       }
       // row jb: wind toward -x
-      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sbk * ld, xl, full, Nx);
-      rp_flux_diff<false>(rb, lane, iws, ws6, dphi);
+      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sbk * ld, xl, full, Nx, out);
+      rp_flux_diff<false>(rb, iws, ws6, dphi);
 #pragma unroll
       for (int q = 0; q < RP_C; ++q) feq[q] = __fsub_rn(E[q], O[q]);
-      rp_finish<S>(A, T, rb, dphi, fn, -cxi, rt0, rt1, -xi, feq, Fout + (size_t)sbk * ld, xl, full, stb);
+      rp_finish<S>(A, T, rb, dphi, fn, -cxi, rt0, rt1, -xi, feq, Fout + (size_t)sbk * ld, xl, full, out, stb);
       if (T.collide) rp_sums_pair(Sm, stf, stb, rv[R_X], rv[R_X + 1], rv[R_X2], rv[R_X2 + 1]);
     }
     if (Qxi & 1) {  // the xi = 0 row: no advection; its equilibrium has only even Legendre terms
@@ -505,9 +520,9 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
           feq[3] = fmaf(b4.w, pk, feq[3]);
         }
       }
-      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sc * ld, xl, full, Nx);
-      rp_finish<S>(A, T, ra, zero, fn, 0.f, rt0, rt1, 0.f, feq, Fout + (size_t)sc * ld, xl, full, st);
-      if (i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)((i + 1) * Qxi + Qxi - 1) * ld, xl, full, csrc, edge, hsrc);
+      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sc * ld, xl, full, Nx, out);
+      rp_finish<S>(A, T, ra, zero, fn, 0.f, rt0, rt1, 0.f, feq, Fout + (size_t)sc * ld, xl, full, out, st);
+      if (i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)((i + 1) * Qxi + Qxi - 1) * ld, xl, full, T);
       if (T.collide) {
 #pragma unroll
         for (int q = 0; q < RP_C; ++q) rlbdev::df_add(Sm.s0[q], {st[q], 0.f});
@@ -523,7 +538,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
   if (T.collide) {
 #pragma unroll
     for (int q = 0; q < RP_C; ++q)
-      if (xl + q < Nx) {
+      if (out && xl + q < Nx) {
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
           const float2 m = M[f * RP_WT + RP_C * lane + q];

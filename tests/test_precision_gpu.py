@@ -151,12 +151,17 @@ def test_mixed_storage_in_one_handle_rejected():
 
 @pytest.mark.parametrize("storage", [rb.STORAGE_F32, rb.STORAGE_BF16])
 def test_orders_and_grids_of_the_warp_tiles(storage):
-    """The reduced-precision kernel's paths in one handle: 128-cell warp tiles that are full, ragged (127,
-    129, 257 cells) or shorter than a tile (60, 9, 3, 2, 1 cells), open and periodic boundaries, odd Qxi (a
-    xi = 0 node), the generic orders (Np = 3, Nv = 8: 9 coefficient columns per radial node), and tubes of
+    """The reduced-precision kernel's paths in one handle: warp tiles of 120 cells (a warp holds 128, the
+    4-cell halo in its edge lanes) whose cells all lie inside the tube (vector loads: the second tile of 244
+    cells ends exactly at the tube's end, 367 has two such tiles), that reach past an end by a cell (243) or
+    more (127, 129, 257), or shorter than a tile (60, 9, 3, 2, 1 cells), open and periodic boundaries, odd Qxi
+    (a xi = 0 node), the generic orders (Np = 3, Nv = 8: 9 coefficient columns per radial node), and tubes of
     different orders sharing the per-warp shared-memory layout."""
     specs = [W.random_smooth(127, 8, 2e-2, seed=11, bc=W.BC_OPEN),
              W.random_smooth(128, 5, 1e-2, seed=12),
+             W.random_smooth(244, 8, 1e-2, seed=20, bc=W.BC_OPEN),
+             W.random_smooth(243, 6, 1e-2, seed=21),
+             W.random_smooth(367, 5, 2e-2, seed=22, bc=W.BC_OPEN),
              W.random_smooth(129, 16, 5e-3, seed=13, bc=W.BC_OPEN),
              W.random_smooth(257, 4, 3e-2, seed=14, Qp=4, Np=3, Nv=5),
              W.random_smooth(60, 6, 1e-2, seed=15, Qp=4, Np=3, Nv=8, bc=W.BC_OPEN),
