@@ -223,8 +223,9 @@ rlb_status rlb_quadrature(int32_t Qp, int32_t Qxi, double *pbar, double *wp, dou
  * Launch shape of a handle's steps (no counterpart in the paper; it changes how the work is scheduled, never
  * the arithmetic: every choice gives bit-identical results).
  *   schedule:     RLB_SCHED_TILE (one CTA per tile, the default), RLB_SCHED_STRIDE (persistent grid, tiles by
- *                 grid stride) or RLB_SCHED_COUNTER (persistent grid, tiles handed out by an atomic counter;
- *                 no CTA waits on another).
+ *                 grid stride) or RLB_SCHED_COUNTER (persistent grid, tiles handed out by an atomic counter:
+ *                 to whole CTAs in the FP64 kernel, to single warps in the reduced-precision kernel, whose
+ *                 tiles are warp tiles; nothing waits on another CTA or warp).
  *   ctas_per_sm:  persistent grid = SMs x ctas_per_sm; 0 takes the occupancy limit.
  *   graph_steps:  rlb_step replays a captured CUDA graph of this many steps (on a private stream joined to the
  *                 handle's stream by events); 0 launches directly. Calls made while the handle's stream is

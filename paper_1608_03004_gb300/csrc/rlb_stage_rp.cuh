@@ -553,15 +553,27 @@ __global__ void __launch_bounds__(RP_NT, 4) rlb_stage_rp_kernel(StageArgsRP A) {
   extern __shared__ __align__(16) float stage_rp_smem[];
   const int warp = threadIdx.x / 32;
   const RpWarp w{stage_rp_smem + (size_t)warp * RP_WT * rp_rows(A.brows)};
+  auto run = [&](int wt) {
+    const int2 tl = A.wtiles[wt];
+    const TubeDev T = A.tubes[tl.x];
+    if (T.Np == 2 && T.Nv == 5)
+      warp_tile_rp<S, 2, 5>(A, T, tl.y, w);
+    else
+      warp_tile_rp<S, NP_MAX, NV_MAX>(A, T, tl.y, w);
+  };
+  if (SCHED == 2) {
+    // counter schedule: every warp takes warp tiles one at a time, so that warps (not CTAs) finish unevenly at
+    // the end of the launch; a warp's shared memory is lane-private, so no barrier separates its tiles
+    for (;;) {
+      int wt = 0;
+      if ((threadIdx.x & 31) == 0) wt = atomicAdd(A.counter, 1);
+      wt = __shfl_sync(0xffffffffu, wt, 0);
+      if (wt >= A.nwt) return;
+      run(wt);
+    }
+  }
   for_each_tile(A.ngroups, SCHED, A.counter, [&](int grp) {
     const int wt = grp * RP_WARPS + warp;
-    if (wt < A.nwt) {  // uniform over the warp
-      const int2 tl = A.wtiles[wt];
-      const TubeDev T = A.tubes[tl.x];
-      if (T.Np == 2 && T.Nv == 5)
-        warp_tile_rp<S, 2, 5>(A, T, tl.y, w);
-      else
-        warp_tile_rp<S, NP_MAX, NV_MAX>(A, T, tl.y, w);
-    }
+    if (wt < A.nwt) run(wt);  // uniform over the warp
   });
 }
