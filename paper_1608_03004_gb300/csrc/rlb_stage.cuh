@@ -358,15 +358,26 @@ __device__ void stage_tile(const StageArgs& A, const TubeDev& T, int x0, int par
       // as well)
       {
         const double* src = Fin + (size_t)s * ld;
-        for (int k = c; k < RW; k += GW) {
+        // positions 0 .. GW-1, one per thread: the previous position's value comes from the lane below by a
+        // shuffle (the first lane of each warp loads it)
+        {
+          const double v = __ldg(src + sm.src[c]);
+          row[c] = v;
+          const double below = __shfl_up_sync(0xffffffffu, v, 1);
+          if (c > 0) {
+            const double dk = v - ((c & 31) == 0 ? __ldg(src + sm.src[c - 1]) : below);
+            d1[c] = dk;
+            const rlbdev::DF q = rlbdev::df_split(dk);
+            dd[c] = make_float2(q.hi, q.lo);
+          }
+        }
+        for (int k = c + GW; k < RW; k += GW) {
           const double v = __ldg(src + sm.src[k]);
           row[k] = v;
-          if (k > 0) {
-            const double dk = v - __ldg(src + sm.src[k - 1]);
-            d1[k] = dk;
-            const rlbdev::DF q = rlbdev::df_split(dk);
-            dd[k] = make_float2(q.hi, q.lo);
-          }
+          const double dk = v - __ldg(src + sm.src[k - 1]);
+          d1[k] = dk;
+          const rlbdev::DF q = rlbdev::df_split(dk);
+          dd[k] = make_float2(q.hi, q.lo);
         }
       }
       // the Runge-Kutta input of this row's cell, loaded now so that its latency hides behind the limiter
