@@ -61,20 +61,7 @@ __device__ __forceinline__ float ld_s<__nv_bfloat16>(const __nv_bfloat16* p) {
   return __uint_as_float((unsigned)u << 16);
 }
 
-// The value a float becomes once stored as S.
-template <typename S>
-__device__ __forceinline__ float rnd_s(float v);
-template <>
-__device__ __forceinline__ float rnd_s<float>(float v) {
-  return v;
-}
-template <>
-__device__ __forceinline__ float rnd_s<__nv_bfloat16>(float v) {
-  return __bfloat162float(__float2bfloat16_rn(v));
-}
-
-// Four consecutive stored values (16-byte aligned in FP32, 8-byte aligned in BF16) and their store; the
-// stored values are already representable in S.
+// Four consecutive stored values (16-byte aligned in FP32, 8-byte aligned in BF16), and their FP32 store.
 __device__ __forceinline__ float4 ld4(const float* p) { return ld_stream4(p); }
 __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
   const uint2 u = ld_stream2(p);
@@ -83,23 +70,6 @@ __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
   return make_float4(a.x, a.y, b.x, b.y);
 }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-__device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
-  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-  uint2 u;
-  u.x = *reinterpret_cast<const unsigned*>(&a);
-  u.y = *reinterpret_cast<const unsigned*>(&b);
-  *reinterpret_cast<uint2*>(p) = u;
-}
-template <typename S>
-__device__ __forceinline__ void st_s(S* p, float v);
-template <>
-__device__ __forceinline__ void st_s<float>(float* p, float v) {
-  *p = v;
-}
-template <>
-__device__ __forceinline__ void st_s<__nv_bfloat16>(__nv_bfloat16* p, float v) {
-  *p = __float2bfloat16_rn(v);
-}
 
 constexpr int RP_C = 4;                   // cells per lane
 constexpr int RP_WT = 32 * RP_C;          // cells a warp holds
@@ -335,6 +305,39 @@ __device__ __forceinline__ void rp_flux_diff(const RpRow& r, float iws, float ws
     dphi[q] = fmaf(__fsub_rn(G6[q + 1], G6[q]), ws6, FWD ? D[q] : (q + 1 < RP_C ? D[q + 1] : D4));
 }
 
+// Round a lane's four outputs to storage in place (the values the next stage reads and the moments sum) and store
+// them if the lane is an output lane; BF16 rounds each pair of values with one packing conversion and stores the
+// packed words.
+__device__ __forceinline__ void rp_round_store(float (&v)[RP_C], float* dst, int xl, bool full, bool out, int Nx) {
+  if (!out) return;
+  if (full) {
+    st4(dst + xl, make_float4(v[0], v[1], v[2], v[3]));
+  } else {
+#pragma unroll
+    for (int q = 0; q < RP_C; ++q)
+      if (xl + q < Nx) dst[xl + q] = v[q];
+  }
+}
+__device__ __forceinline__ void rp_round_store(float (&v)[RP_C], __nv_bfloat16* dst, int xl, bool full, bool out,
+                                               int Nx) {
+  const __nv_bfloat162 p01 = __floats2bfloat162_rn(v[0], v[1]), p23 = __floats2bfloat162_rn(v[2], v[3]);
+  const unsigned u01 = *reinterpret_cast<const unsigned*>(&p01), u23 = *reinterpret_cast<const unsigned*>(&p23);
+  v[0] = __uint_as_float(u01 << 16);
+  v[1] = __uint_as_float(u01 & 0xffff0000u);
+  v[2] = __uint_as_float(u23 << 16);
+  v[3] = __uint_as_float(u23 & 0xffff0000u);
+  if (!out) return;
+  if (full) {
+    *reinterpret_cast<uint2*>(dst + xl) = make_uint2(u01, u23);
+  } else {
+    const unsigned short h[RP_C] = {(unsigned short)(u01 & 0xffffu), (unsigned short)(u01 >> 16),
+                                    (unsigned short)(u23 & 0xffffu), (unsigned short)(u23 >> 16)};
+#pragma unroll
+    for (int q = 0; q < RP_C; ++q)
+      if (xl + q < Nx) reinterpret_cast<unsigned short*>(dst)[xl + q] = h[q];
+  }
+}
+
 // F_out = a F^n + b F - cxi dphi + rate (feq - F) of a lane's cells, rounded to storage and stored by the output
 // lanes (out); returns the values in st.
 template <typename S>
@@ -349,16 +352,9 @@ __device__ __forceinline__ void rp_finish(const StageArgsRP& A, const TubeDev& T
     float o = A.a != 0.f ? fmaf(A.a, fn[q], __fmul_rn(A.b, F)) : F;
     o = fmaf(-cxi, dphi[q], o);
     if (T.collide) o = fmaf(fmaf(-rt1[q], xi, rt0[q]), __fsub_rn(feq[q], F), o);
-    st[q] = rnd_s<S>(o);
+    st[q] = o;
   }
-  if (!out) return;
-  if (full) {
-    st4(dst + xl, make_float4(st[0], st[1], st[2], st[3]));
-  } else {
-#pragma unroll
-    for (int q = 0; q < RP_C; ++q)
-      if (xl + q < T.Nx) st_s<S>(dst + xl + q, st[q]);
-  }
+  rp_round_store(st, dst, xl, full, out, T.Nx);
 }
 
 // The compensated radial sums of one radial node i over the directions walked so far, per cell:
