@@ -465,9 +465,16 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
                                 r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
       const float xi = rv[R_XI], cxi = A.stage == 0 ? rv[R_CXI] : (A.stage == 1 ? rv[R_CXI + 1] : rv[R_CXI + 2]);
       const float iws = rv[R_IWS], ws6 = rv[R_WS6];
-      float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C], dphi[RP_C], stf[RP_C], stb[RP_C];
+      float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, fnb[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C], dphi[RP_C], stf[RP_C],
+            stb[RP_C];
+      // F^n of both rows: in FP32 both loaded now, a whole row's evaluation ahead of the second row's use
+      // (measured 7 % faster); in BF16 the second row's just before its flux differences (1.5 % faster there)
+      constexpr bool early = std::is_same<S, float>::value;
+      if (A.a != 0.f) {
+        rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx, out);
+        if (early) rp_load_fn<S>(fnb, Fn, (size_t)sbk * ld, xl, full, Nx, out);
+      }
       // row jf: wind toward +x
-      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx, out);
       rp_flux_diff<true>(ra, iws, ws6, dphi);
       // even and odd Legendre parts of the pair's equilibria: feq(+xi) = E + O, feq(-xi) = E - O
       float E[RP_C] = {0.f, 0.f, 0.f, 0.f}, O[RP_C] = {0.f, 0.f, 0.f, 0.f};
@@ -491,11 +498,11 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
         if (jb + 1 < hq || (Qxi & 1) || i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)snx * ld, xl, full, T);
       }
       // row jb: wind toward -x
-      if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sbk * ld, xl, full, Nx, out);
+      if (!early && A.a != 0.f) rp_load_fn<S>(fnb, Fn, (size_t)sbk * ld, xl, full, Nx, out);
       rp_flux_diff<false>(rb, iws, ws6, dphi);
 #pragma unroll
       for (int q = 0; q < RP_C; ++q) feq[q] = __fsub_rn(E[q], O[q]);
-      rp_finish<S>(A, T, rb, dphi, fn, -cxi, rt0, rt1, -xi, feq, Fout + (size_t)sbk * ld, xl, full, out, stb);
+      rp_finish<S>(A, T, rb, dphi, fnb, -cxi, rt0, rt1, -xi, feq, Fout + (size_t)sbk * ld, xl, full, out, stb);
       if (T.collide) rp_sums_pair(Sm, stf, stb, rv[R_X], rv[R_X + 1], rv[R_X2], rv[R_X2 + 1]);
     }
     if (Qxi & 1) {  // the xi = 0 row: no advection; its equilibrium has only even Legendre terms
