@@ -49,26 +49,7 @@ __device__ __forceinline__ uint2 ld_stream2(const void* p) {
   return v;
 }
 
-template <typename S>
-__device__ __forceinline__ float ld_s(const S* p);
-template <>
-__device__ __forceinline__ float ld_s<float>(const float* p) {
-  return ld_stream(p);
-}
-template <>
-__device__ __forceinline__ float ld_s<__nv_bfloat16>(const __nv_bfloat16* p) {
-  const unsigned short u = ld_stream(reinterpret_cast<const unsigned short*>(p));
-  return __uint_as_float((unsigned)u << 16);
-}
-
-// Four consecutive stored values (16-byte aligned in FP32, 8-byte aligned in BF16), and their FP32 store.
-__device__ __forceinline__ float4 ld4(const float* p) { return ld_stream4(p); }
-__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
-  const uint2 u = ld_stream2(p);
-  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
-  return make_float4(a.x, a.y, b.x, b.y);
-}
+// The FP32 store of four consecutive values (16-byte aligned).
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
 constexpr int RP_C = 4;                   // cells per lane
@@ -189,43 +170,79 @@ __device__ void cell_coeffs_rp(const TubeDev* Tg, const double* tab, int Qp, con
 }
 
 // One velocity row as a lane holds it: its RP_C cells xl .. xl+3 (xl = x0 - RP_C + RP_C lane, so that lane 0
-// holds the tile's left halo x0-4 .. x0-1 and lane 31 its right halo x0+RP_OUT .. +3).
-struct RpRow {
+// holds the tile's left halo x0-4 .. x0-1 and lane 31 its right halo x0+RP_OUT .. +3), as stored: FP32 values,
+// or BF16 values two to a word, widened (exactly) only where they are used, so that a warp does not wait for a
+// load it issued a row ahead at the load itself.
+template <typename S>
+struct RpRow;
+template <>
+struct RpRow<float> {
   float v[RP_C];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < RP_C; ++q) v[q] = 0.f;
+  }
+  __device__ __forceinline__ void ld4(const float* p) {
+    const float4 t = ld_stream4(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+  __device__ __forceinline__ void ld1(int q, const float* p) { v[q] = ld_stream(p); }
+  __device__ __forceinline__ void get(float (&o)[RP_C]) const {
+#pragma unroll
+    for (int q = 0; q < RP_C; ++q) o[q] = v[q];
+  }
+};
+template <>
+struct RpRow<__nv_bfloat16> {
+  unsigned u[2];  // cells 0, 1 in u[0] and 2, 3 in u[1], the lower address in the low half
+  __device__ __forceinline__ void zero() { u[0] = u[1] = 0u; }
+  __device__ __forceinline__ void ld4(const __nv_bfloat16* p) {
+    const uint2 t = ld_stream2(p);
+    u[0] = t.x;
+    u[1] = t.y;
+  }
+  __device__ __forceinline__ void ld1(int q, const __nv_bfloat16* p) {
+    const unsigned h = ld_stream(reinterpret_cast<const unsigned short*>(p));
+    u[q >> 1] = (q & 1) ? ((u[q >> 1] & 0xffffu) | (h << 16)) : ((u[q >> 1] & 0xffff0000u) | h);
+  }
+  __device__ __forceinline__ void get(float (&o)[RP_C]) const {
+    o[0] = __uint_as_float(u[0] << 16);
+    o[1] = __uint_as_float(u[0] & 0xffff0000u);
+    o[2] = __uint_as_float(u[1] << 16);
+    o[3] = __uint_as_float(u[1] & 0xffff0000u);
+  }
 };
 
 // A row's cells: one vector load where the warp's 128 cells all lie inside the tube (full), otherwise one load
 // per cell from its source under the boundary condition (positions left of -3 are never used and read -3).
 template <typename S>
-__device__ __forceinline__ void rp_load_row(RpRow& r, const S* Fin, size_t row, int xl, bool full, const TubeDev& T) {
+__device__ __forceinline__ void rp_load_row(RpRow<S>& r, const S* Fin, size_t row, int xl, bool full,
+                                            const TubeDev& T) {
   const S* src = Fin + row;
   if (full) {
-    const float4 t = ld4(src + xl);
-    r.v[0] = t.x;
-    r.v[1] = t.y;
-    r.v[2] = t.z;
-    r.v[3] = t.w;
+    r.ld4(src + xl);
   } else {
+    r.zero();
 #pragma unroll
-    for (int q = 0; q < RP_C; ++q) r.v[q] = ld_s<S>(src + map_cell(max(xl + q, -HALO), T.Nx, T.bc, T.ld));
+    for (int q = 0; q < RP_C; ++q) r.ld1(q, src + map_cell(max(xl + q, -HALO), T.Nx, T.bc, T.ld));
   }
 }
 
-// F^n of a lane's cells (stages 2 and 3 only; output lanes only, whose cells are >= 0).
+// F^n of a lane's cells (stages 2 and 3 only; output lanes only, whose cells are >= 0); fn starts zeroed.
 template <typename S>
-__device__ __forceinline__ void rp_load_fn(float (&fn)[RP_C], const S* Fn, size_t row, int xl, bool full, int Nx,
+__device__ __forceinline__ void rp_load_fn(RpRow<S>& fn, const S* Fn, size_t row, int xl, bool full, int Nx,
                                            bool out) {
   const S* fs = Fn + row;
   if (!out) return;
   if (full) {
-    const float4 t = ld4(fs + xl);
-    fn[0] = t.x;
-    fn[1] = t.y;
-    fn[2] = t.z;
-    fn[3] = t.w;
+    fn.ld4(fs + xl);
   } else {
 #pragma unroll
-    for (int q = 0; q < RP_C; ++q) fn[q] = (xl + q < Nx) ? ld_s<S>(fs + xl + q) : 0.f;
+    for (int q = 0; q < RP_C; ++q)
+      if (xl + q < Nx) fn.ld1(q, fs + xl + q);
   }
 }
 
@@ -258,12 +275,12 @@ __device__ __forceinline__ float weno5_square_c(float x, float y) {
 // the differences -D(X+2 .. X-1) in wind order. The edge lanes' own outputs are wrong (no neighbour beyond) and
 // unused: what lanes 1 and 30 take from them involves their own cells only.
 template <bool FWD>
-__device__ __forceinline__ void rp_flux_diff(const RpRow& r, float iws, float ws6, float (&dphi)[RP_C]) {
+__device__ __forceinline__ void rp_flux_diff(const float (&f)[RP_C], float iws, float ws6, float (&dphi)[RP_C]) {
   constexpr unsigned ALL = 0xffffffffu;
   float D[RP_C], dd[RP_C];
-  D[0] = __fsub_rn(r.v[0], __shfl_up_sync(ALL, r.v[3], 1));
+  D[0] = __fsub_rn(f[0], __shfl_up_sync(ALL, f[3], 1));
 #pragma unroll
-  for (int q = 1; q < RP_C; ++q) D[q] = __fsub_rn(r.v[q], r.v[q - 1]);
+  for (int q = 1; q < RP_C; ++q) D[q] = __fsub_rn(f[q], f[q - 1]);
 #pragma unroll
   for (int q = 0; q < RP_C; ++q) dd[q] = __fmul_rn(D[q], iws);
   // D(xl+4), D(xl+5) (and toward -x D(xl+6)) from the right lane, scaled here as that lane scales them
@@ -341,14 +358,16 @@ __device__ __forceinline__ void rp_round_store(float (&v)[RP_C], __nv_bfloat16* 
 // F_out = a F^n + b F - cxi dphi + rate (feq - F) of a lane's cells, rounded to storage and stored by the output
 // lanes (out); returns the values in st.
 template <typename S>
-__device__ __forceinline__ void rp_finish(const StageArgsRP& A, const TubeDev& T, const RpRow& r,
-                                          const float (&dphi)[RP_C], const float (&fn)[RP_C], float cxi,
+__device__ __forceinline__ void rp_finish(const StageArgsRP& A, const TubeDev& T, const float (&f)[RP_C],
+                                          const float (&dphi)[RP_C], const RpRow<S>& fnr, float cxi,
                                           const float (&rt0)[RP_C], const float (&rt1)[RP_C], float xi,
                                           const float (&feq)[RP_C], S* dst, int xl, bool full, bool out,
                                           float (&st)[RP_C]) {
+  float fn[RP_C];
+  fnr.get(fn);
 #pragma unroll
   for (int q = 0; q < RP_C; ++q) {
-    const float F = r.v[q];
+    const float F = f[q];
     float o = A.a != 0.f ? fmaf(A.a, fn[q], __fmul_rn(A.b, F)) : F;
     o = fmaf(-cxi, dphi[q], o);
     if (T.collide) o = fmaf(fmaf(-rt1[q], xi, rt0[q]), __fsub_rn(feq[q], F), o);
@@ -438,7 +457,7 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
   // row. The next row's loads are in flight while a row is evaluated; the walk advances by increments (no
   // division by Qxi per row).
   const int hq = Qxi / 2;
-  RpRow ra, rb;
+  RpRow<S> ra, rb;
   rp_load_row<S>(ra, Fin, (size_t)(Qxi - 1) * ld, xl, full, T);  // the walk's first row
   // The record's second float4 (1/ws, ws/6), which the first row of a pair needs at once, is loaded one pair
   // ahead; the rest of the record is needed only after that row's flux differences, which cover its latency.
@@ -465,17 +484,18 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
                                 r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
       const float xi = rv[R_XI], cxi = A.stage == 0 ? rv[R_CXI] : (A.stage == 1 ? rv[R_CXI + 1] : rv[R_CXI + 2]);
       const float iws = rv[R_IWS], ws6 = rv[R_WS6];
-      float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, fnb[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C], dphi[RP_C], stf[RP_C],
-            stb[RP_C];
-      // F^n of both rows: in FP32 both loaded now, a whole row's evaluation ahead of the second row's use
-      // (measured 7 % faster); in BF16 the second row's just before its flux differences (1.5 % faster there)
-      constexpr bool early = std::is_same<S, float>::value;
+      float feq[RP_C], dphi[RP_C], stf[RP_C], stb[RP_C], fv[RP_C];
+      // F^n of both rows, loaded now: a whole row's evaluation ahead of the second row's use
+      RpRow<S> fn, fnb;
+      fn.zero();
+      fnb.zero();
       if (A.a != 0.f) {
         rp_load_fn<S>(fn, Fn, (size_t)sf * ld, xl, full, Nx, out);
-        if (early) rp_load_fn<S>(fnb, Fn, (size_t)sbk * ld, xl, full, Nx, out);
+        rp_load_fn<S>(fnb, Fn, (size_t)sbk * ld, xl, full, Nx, out);
       }
       // row jf: wind toward +x
-      rp_flux_diff<true>(ra, iws, ws6, dphi);
+      ra.get(fv);
+      rp_flux_diff<true>(fv, iws, ws6, dphi);
       // even and odd Legendre parts of the pair's equilibria: feq(+xi) = E + O, feq(-xi) = E - O
       float E[RP_C] = {0.f, 0.f, 0.f, 0.f}, O[RP_C] = {0.f, 0.f, 0.f, 0.f};
       if (T.collide) {
@@ -492,17 +512,17 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       }
 #pragma unroll
       for (int q = 0; q < RP_C; ++q) feq[q] = __fadd_rn(E[q], O[q]);
-      rp_finish<S>(A, T, ra, dphi, fn, cxi, rt0, rt1, xi, feq, Fout + (size_t)sf * ld, xl, full, out, stf);
+      rp_finish<S>(A, T, fv, dphi, fn, cxi, rt0, rt1, xi, feq, Fout + (size_t)sf * ld, xl, full, out, stf);
       {
         const int snx = jb + 1 < hq ? sf - 1 : ((Qxi & 1) ? i * Qxi + hq : (i + 1) * Qxi + Qxi - 1);
         if (jb + 1 < hq || (Qxi & 1) || i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)snx * ld, xl, full, T);
       }
       // row jb: wind toward -x
-      if (!early && A.a != 0.f) rp_load_fn<S>(fnb, Fn, (size_t)sbk * ld, xl, full, Nx, out);
-      rp_flux_diff<false>(rb, iws, ws6, dphi);
+      rb.get(fv);
+      rp_flux_diff<false>(fv, iws, ws6, dphi);
 #pragma unroll
       for (int q = 0; q < RP_C; ++q) feq[q] = __fsub_rn(E[q], O[q]);
-      rp_finish<S>(A, T, rb, dphi, fnb, -cxi, rt0, rt1, -xi, feq, Fout + (size_t)sbk * ld, xl, full, out, stb);
+      rp_finish<S>(A, T, fv, dphi, fnb, -cxi, rt0, rt1, -xi, feq, Fout + (size_t)sbk * ld, xl, full, out, stb);
       if (T.collide) rp_sums_pair(Sm, stf, stb, rv[R_X], rv[R_X + 1], rv[R_X2], rv[R_X2 + 1]);
     }
     if (Qxi & 1) {  // the xi = 0 row: no advection; its equilibrium has only even Legendre terms
@@ -510,8 +530,10 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
       const float4* rp = rec + (size_t)sc * (RP_REC / 4);
       const float4 r3 = rp[3], r4 = rp[4], r5 = rp[5];
       const float pw[RP_REC - 12] = {r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
-      float fn[RP_C] = {0.f, 0.f, 0.f, 0.f}, feq[RP_C] = {0.f, 0.f, 0.f, 0.f}, st[RP_C];
+      float feq[RP_C] = {0.f, 0.f, 0.f, 0.f}, st[RP_C], fv[RP_C];
       const float zero[RP_C] = {0.f, 0.f, 0.f, 0.f};
+      RpRow<S> fn;
+      fn.zero();
       if (T.collide) {
 #pragma unroll
         for (int kk = 0; kk <= NVc; kk += 2) {
@@ -524,7 +546,8 @@ __device__ void warp_tile_rp(const StageArgsRP& A, const TubeDev& T, int x0, con
         }
       }
       if (A.a != 0.f) rp_load_fn<S>(fn, Fn, (size_t)sc * ld, xl, full, Nx, out);
-      rp_finish<S>(A, T, ra, zero, fn, 0.f, rt0, rt1, 0.f, feq, Fout + (size_t)sc * ld, xl, full, out, st);
+      ra.get(fv);
+      rp_finish<S>(A, T, fv, zero, fn, 0.f, rt0, rt1, 0.f, feq, Fout + (size_t)sc * ld, xl, full, out, st);
       if (i + 1 < Qp) rp_load_row<S>(ra, Fin, (size_t)((i + 1) * Qxi + Qxi - 1) * ld, xl, full, T);
       if (T.collide) {
 #pragma unroll
