@@ -641,6 +641,57 @@ def extras(args, rank, world, head):
     return out
 
 
+def run_slabs(args, specs, desc):
+    """The stress tube split into args.slabs x-slabs on this one GPU (one handle per slab), advanced by the
+    decomposition's data path: before every Runge-Kutta stage each slab packs its edge cells, the blocks go to
+    the neighbours' receive buffers by device copies, the ghosts are unpacked, then the stage runs. The result is
+    bit-identical to the undivided tube (tests/test_decompose_gpu.py), so the gap to the undivided tube's rate
+    is the cost of the exchange and of launching per slab. Same metric; one JSON line."""
+    import torch
+
+    from paper_1608_03004_gb300 import binding as rb
+    from paper_1608_03004_gb300 import decompose as D
+
+    (s,) = specs
+    x = s.x_left + (np.arange(s.Nx) + 0.5) * s.dx
+    P, n, v = (np.where(x < 0, s.left[k], s.right[k]).astype(np.float64) for k in range(3))
+    tube = rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, s.tau, s.bc, rb.STORAGE[args.precision])
+    tubes, bounds, sched = D.slab_tubes(tube, args.slabs)
+    handles = [rb.rlb_init([t], P[a:b], n[a:b], v[a:b]) for t, (a, b) in zip(tubes, bounds)]
+    dtype = rb.halo_dtype(handles[0])
+    sends = [torch.zeros(rb.rlb_halo_size(h), dtype=dtype, device="cuda") for h in handles]
+    recvs = [torch.zeros_like(t) for t in sends]
+    ex = D.LocalExchange(sched, 3 * s.Q)
+    D.step_slabs(handles, ex, sends, recvs, args.warmup)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    clocks = ClockSampler(int(visible[0]) if visible[0].isdigit() else 0)
+    e0.record(stream)
+    D.step_slabs(handles, ex, sends, recvs, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    for h in handles:
+        rb.rlb_sync(h)
+        rb.rlb_destroy(h)
+    ms = e0.elapsed_time(e1) / args.steps
+    nodes = W.total_nodes(specs)
+    esize = ESIZE[args.precision]
+    print(json.dumps({
+        "metric": METRIC, "value": nodes / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": desc, "slabs": args.slabs, "slab_cells": [b - a for a, b in bounds],
+                   "exchange": "before every stage: rlb_halo_pack, device copies of 3 Q cells per side, "
+                               "rlb_halo_unpack, then rlb_stage per slab",
+                   "halo_bytes_per_boundary_and_stage": 2 * 3 * s.Q * esize,
+                   "parallelism": f"{args.slabs} x-slabs of one tube on one GPU"},
+        "clocks": clk, "gpu_launches": 3 * args.steps * (3 * args.slabs),
+    }), flush=True)
+
+
 def run_gradient(args, specs, desc, rank, world, emit=True):
     """Gradients of the inverse problem through the adjoint: each step is one full gradient (set the initial
     state, rlb_record, the loss's seed, rlb_backward, rlb_init_vjp)."""
@@ -802,6 +853,8 @@ def main():
                     "(default 50; >= 1000 keeps every stage input and recomputes nothing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="time the headline workload only")
+    ap.add_argument("--slabs", type=int, default=0, help="with --workload stress: split the tube into this many "
+                    "x-slabs on this GPU and time the decomposition's data path (halo exchange before every stage)")
     args = ap.parse_args()
     args.extras = args.workload is None and not args.no_extras
     if args.workload is None:
@@ -829,7 +882,11 @@ def main():
     else:
         torch.cuda.set_device(0)
     try:
-        if args.workload.startswith("gradient"):
+        if args.slabs > 1:
+            if args.workload != "stress" or world > 1:
+                raise SystemExit("--slabs takes --workload stress on one GPU")
+            run_slabs(args, specs, desc)
+        elif args.workload.startswith("gradient"):
             run_gradient(args, specs, desc, rank, world)
         else:
             run_ours(args, specs, desc, rank, world)
