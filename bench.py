@@ -646,7 +646,9 @@ def run_slabs(args, specs, desc):
     decomposition's data path: before every Runge-Kutta stage each slab packs its edge cells, the blocks go to
     the neighbours' receive buffers by device copies, the ghosts are unpacked, then the stage runs. The result is
     bit-identical to the undivided tube (tests/test_decompose_gpu.py), so the gap to the undivided tube's rate
-    is the cost of the exchange and of launching per slab. Same metric; one JSON line."""
+    is the cost of the exchange and of launching per slab. The steps are timed twice: launched one call at a
+    time from the host, then as a captured CUDA graph of one step replayed (decompose.GraphStep); `value` is the
+    graph's. Same metric; one JSON line."""
     import torch
 
     from paper_1608_03004_gb300 import binding as rb
@@ -657,26 +659,35 @@ def run_slabs(args, specs, desc):
     P, n, v = (np.where(x < 0, s.left[k], s.right[k]).astype(np.float64) for k in range(3))
     tube = rb.Tube(s.Qp, s.Qxi, s.Np, s.Nv, s.Nx, s.dx, s.dt, s.tau, s.bc, rb.STORAGE[args.precision])
     tubes, bounds, sched = D.slab_tubes(tube, args.slabs)
-    handles = [rb.rlb_init([t], P[a:b], n[a:b], v[a:b]) for t, (a, b) in zip(tubes, bounds)]
+    stream = torch.cuda.Stream()
+    handles = [rb.rlb_init([t], P[a:b], n[a:b], v[a:b], stream=stream.cuda_stream) for t, (a, b) in zip(tubes, bounds)]
     dtype = rb.halo_dtype(handles[0])
     sends = [torch.zeros(rb.rlb_halo_size(h), dtype=dtype, device="cuda") for h in handles]
     recvs = [torch.zeros_like(t) for t in sends]
     ex = D.LocalExchange(sched, 3 * s.Q)
-    D.step_slabs(handles, ex, sends, recvs, args.warmup)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
     clocks = ClockSampler(int(visible[0]) if visible[0].isdigit() else 0)
-    e0.record(stream)
-    D.step_slabs(handles, ex, sends, recvs, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+
+    def timed(run):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    with torch.cuda.stream(stream):
+        D.step_slabs(handles, ex, sends, recvs, args.warmup)
+        ms_launched = timed(lambda k: D.step_slabs(handles, ex, sends, recvs, k))
+    graph = D.GraphStep(handles, ex, sends, recvs, stream)
+    graph(args.warmup)
+    ms = timed(graph)
     clk = clocks.stop()
     for h in handles:
         rb.rlb_sync(h)
         rb.rlb_destroy(h)
-    ms = e0.elapsed_time(e1) / args.steps
     nodes = W.total_nodes(specs)
     esize = ESIZE[args.precision]
     print(json.dumps({
@@ -687,8 +698,9 @@ def run_slabs(args, specs, desc):
                    "exchange": "before every stage: rlb_halo_pack, device copies of 3 Q cells per side, "
                                "rlb_halo_unpack, then rlb_stage per slab",
                    "halo_bytes_per_boundary_and_stage": 2 * 3 * s.Q * esize,
+                   "ms_per_step_launched": ms_launched, "ms_per_step_graph": ms,
                    "parallelism": f"{args.slabs} x-slabs of one tube on one GPU"},
-        "clocks": clk, "gpu_launches": 3 * args.steps * (3 * args.slabs),
+        "clocks": clk, "gpu_launches": 3 * args.steps * (3 * args.slabs),  # packs, unpacks, stages (+ copies)
     }), flush=True)
 
 
